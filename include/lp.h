@@ -1,0 +1,210 @@
+/*
+ * lp.h -- C ABI of liblp, GPU (sm_103a) neighbourhood-based link prediction.
+ *
+ * The library implements the scoring and selection of "A Fast Parallel
+ * Approach for Neighborhood-based Link Prediction by Disregarding Large Hubs"
+ * (Sahu, arXiv 2401.11415):
+ *   - IBase (Section 4.1): for every source vertex a, the second-order
+ *     vertices c reachable as a -> b -> c are scored; first-order neighbours
+ *     and c = a are never predicted (Sections 4.1.1, 4.1.2, 4.1.4).
+ *   - DLH (Section 4.2, Algorithm 1): the same, but an intermediary b is
+ *     used only when |Gamma_b| <= L_H (the hub limit, inclusive).
+ *   - Scores: the nine measures of Section 3.1 (Eq. 1-9).  AA and RA sum over
+ *     the common neighbours b (as Algorithm 1 accumulates them) with the
+ *     natural logarithm.  The normalisations use full degrees; under DLH, CN
+ *     counts only the intermediaries that pass the hub limit.
+ *   - Selection: the N_P best pairs with a score strictly above S_th
+ *     (Section 4.3 and Algorithm 1), or the k best partners of each requested
+ *     source (a per-vertex form of the ranked top-k list of Section 3).
+ *
+ * Conventions for every call:
+ *   - All pointers are HOST pointers unless the name says "_dev"/"d_" (a
+ *     CUDA device pointer on the graph's device).  Inputs are copied; the
+ *     caller keeps ownership of everything it passes in.  Outputs go into
+ *     caller-owned buffers.
+ *   - Calls are synchronous and thread-safe: a graph is immutable after
+ *     creation and may be shared by threads; calls on one graph serialise
+ *     on that graph's CUDA stream.  No call aborts the process: each returns
+ *     an lp_status and sets a thread-local message (lp_last_error).
+ *   - Results are deterministic: ties are broken by one total order, higher
+ *     score first, then smaller u, then smaller v (per-source: smaller v).
+ *     The seven count measures are ordered by their exact rational value
+ *     (Salton through CN^2 / (|Gamma_a| |Gamma_c|)); AA and RA by their
+ *     fixed-point sums (each weight rounded to 2^-F, F >= 40, then summed
+ *     exactly), which agree with FP64 sums to better than 1e-9 relative.
+ */
+#ifndef LP_H
+#define LP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque device-resident graph (CSR, sorted adjacency, per-arc table). */
+typedef struct lp_graph lp_graph;
+/* Opaque request server (continuous batching of per-source queries). */
+typedef struct lp_server lp_server;
+
+/* Similarity measures, Eq. 1-9 of Section 3.1. */
+typedef enum {
+  LP_CN = 0,  /* common neighbours |Ga n Gc|                         (Eq. 1) */
+  LP_JC = 1,  /* Jaccard CN / (|Ga| + |Gc| - CN)                      (Eq. 2) */
+  LP_SI = 2,  /* Sorensen CN / (|Ga| + |Gc|)                          (Eq. 3) */
+  LP_SC = 3,  /* Salton CN / sqrt(|Ga| |Gc|)                          (Eq. 4) */
+  LP_HP = 4,  /* hub promoted CN / min(|Ga|, |Gc|)                    (Eq. 5) */
+  LP_HD = 5,  /* hub depressed CN / max(|Ga|, |Gc|)                   (Eq. 6) */
+  LP_LHN = 6, /* Leicht-Holme-Newman CN / (|Ga| |Gc|)                 (Eq. 7) */
+  LP_AA = 7,  /* Adamic-Adar sum over common b of 1 / ln |Gb|         (Eq. 8) */
+  LP_RA = 8   /* resource allocation sum over common b of 1 / |Gb|    (Eq. 9) */
+} lp_measure;
+
+typedef enum {
+  LP_OK = 0,
+  LP_EINVAL = 1,    /* bad argument or malformed graph */
+  LP_ENOMEM = 2,    /* device or host allocation failed */
+  LP_ECUDA = 3,     /* a CUDA call failed */
+  LP_ETRUNC = 4,    /* output buffer too small: first out_cap links written */
+  LP_ETIMEOUT = 5,  /* a bounded wait ran out */
+  LP_EBUSY = 6,     /* queue full or object in use */
+  LP_EINTERNAL = 7  /* a device-side consistency check failed */
+} lp_status;
+
+/* One predicted link.  Global mode: u < v.  Per-source mode: u = source.
+ * score: the FP32 value of the measure; cn: common neighbours b of (u, v)
+ * with |Gamma_b| <= degree_cap. */
+typedef struct {
+  int32_t u, v;
+  float score;
+  int32_t cn;
+} lp_link;
+
+#define LP_CAP_NONE (-1)          /* degree_cap for IBase (no hub limit) */
+#define LP_MAX_TOPK_PER_SOURCE 64
+#define LP_VALIDATE_FULL 1u       /* lp_graph_create: also check on the host */
+
+/* Statistics of the last lp_predict / lp_predict_sources call on this thread. */
+typedef struct {
+  int64_t wedges;          /* (a, b, c) triples scanned: b passes the hub test,
+                              c > a (global) or c != a (per-source)            */
+  int64_t kept_arcs;       /* (a, b) arcs of scanned sources passing the hub test */
+  int64_t scanned_arcs;    /* (a, b) arcs read (hub test included)            */
+  int64_t candidates;      /* distinct (a, c) scored                          */
+  int64_t admitted;        /* candidates written to the selection buffer      */
+  int32_t warp_sources;    /* sources scanned by one warp                     */
+  int32_t cta_items;       /* (source, vertex range) items scanned by one CTA */
+  int32_t dense_items;     /* of which dense-counter items                    */
+  int32_t splits;          /* items re-split after a hash overflow            */
+  int32_t compactions;     /* selection-buffer compactions                    */
+  int32_t launches;        /* kernels launched                                */
+  float ms_estimate;       /* device time per phase (0 unless timing enabled) */
+  float ms_scan;
+  float ms_select;
+  float ms_total;
+  /* per scan kernel: [0] warp tier, [1] CTA items */
+  int64_t tier_wedges[2];  /* wedges of the sources binned to the tier       */
+  int64_t tier_arcs[2];    /* arc-table entries read by the tier             */
+  int64_t tier_kept[2];    /* of which pass the hub test                     */
+  int32_t tier_launches[2];/* launches of the tier's scan kernel             */
+  float tier_ms[2];        /* summed device time of those launches (timing on) */
+} lp_stats;
+
+/*
+ * Upload an undirected graph and make it resident on the current CUDA device.
+ *   n        number of vertices (>= 0)
+ *   offsets  host int32[n + 1], offsets[0] = 0, non-decreasing,
+ *            offsets[n] = number of arcs A < 2^31
+ *   indices  host int32[A]: neighbours of v are indices[offsets[v] ..
+ *            offsets[v+1]); every edge must appear in both directions
+ *   flags    LP_VALIDATE_FULL or 0 (the device always checks symmetry)
+ *   out      receives the graph handle
+ * Lists need not be sorted (the library sorts copies).  Rejected with
+ * LP_EINVAL: non-monotone offsets, out-of-range indices, self-loops,
+ * duplicate arcs, a missing reverse arc.  The input model is the paper's
+ * undirected 32-bit-id graph (Section 5.1.2, Table 1).
+ */
+lp_status lp_graph_create(int32_t n, const int32_t* offsets, const int32_t* indices,
+                          uint32_t flags, lp_graph** out);
+
+/* Free a graph.  NULL is accepted. */
+lp_status lp_graph_destroy(lp_graph* g);
+
+/* Vertex count, arc count and largest degree of a graph. */
+lp_status lp_graph_info(const lp_graph* g, int32_t* n, int64_t* arcs, int32_t* max_degree);
+
+/*
+ * Global mode (Algorithm 1, predictLinksDLH): the k best pairs (u < v, not
+ * adjacent, at least one common neighbour through the hub limit) whose score
+ * is strictly above `threshold` (S_th), sorted by the total order.
+ *   degree_cap  L_H, or LP_CAP_NONE (any negative value) for IBase;
+ *               0 gives an empty result
+ *   k           N_P, the maximum number of links; 0 = all of them
+ *   out         host lp_link[out_cap]
+ *   out_n       receives the number of links found (<= k when k > 0)
+ * If out_cap < found, the first out_cap links are written, *out_n = found,
+ * and LP_ETRUNC is returned.
+ */
+lp_status lp_predict(const lp_graph* g, lp_measure measure, int32_t degree_cap, int64_t k,
+                     double threshold, lp_link* out, int64_t out_cap, int64_t* out_n);
+
+/* As lp_predict, but `d_out` is a device pointer (lp_link[out_cap]) on the
+ * graph's device; nothing is copied to the host except *out_n. */
+lp_status lp_predict_dev(const lp_graph* g, lp_measure measure, int32_t degree_cap, int64_t k,
+                         double threshold, lp_link* d_out, int64_t out_cap, int64_t* out_n);
+
+/*
+ * Per-source mode: for each sources[i], its k best partners c != sources[i]
+ * that are not adjacent to it and score strictly above `threshold`, sorted by
+ * (score desc, c asc).  out holds n_src * k links (row i for sources[i]);
+ * counts[i] receives the number written to row i (<= k).  1 <= k <=
+ * LP_MAX_TOPK_PER_SOURCE.  Sources may repeat.  Host pointers.
+ */
+lp_status lp_predict_sources(const lp_graph* g, lp_measure measure, int32_t degree_cap,
+                             const int32_t* sources, int32_t n_src, int32_t k,
+                             double threshold, lp_link* out, int32_t* counts);
+
+/* As lp_predict_sources with device pointers for sources, out and counts. */
+lp_status lp_predict_sources_dev(const lp_graph* g, lp_measure measure, int32_t degree_cap,
+                                 const int32_t* d_sources, int32_t n_src, int32_t k,
+                                 double threshold, lp_link* d_out, int32_t* d_counts);
+
+/* Tuning options (process-wide; each applies to calls that start after it is
+ * set).  They change speed and memory use, never results. */
+typedef enum {
+  LP_OPT_SELECT_BUFFER = 1,   /* minimum selection-buffer capacity in candidates
+                                 (default 8388608; 24 bytes each, twice)       */
+  LP_OPT_WARP_MAX_WEDGES = 2, /* warp tier: sources with W <= this (1..512, 512) */
+  LP_OPT_CTA_MAX_WEDGES = 3,  /* one CTA item per source up to W (513..8192, 8192) */
+  LP_OPT_SPLIT_TARGET = 4,    /* wedges per split hash item (256..12288, 6144) */
+  LP_OPT_SPLIT_LOGCAP = 5     /* log2 slots of a split hash item (6..14, 14)     */
+} lp_option;
+
+/* Set a tuning option; LP_EINVAL if the option or value is out of range. */
+lp_status lp_set_option(lp_option option, int64_t value);
+
+/* Current value of a tuning option (-1 if unknown). */
+int64_t lp_get_option(lp_option option);
+
+/* Statistics of this thread's last predict call. */
+lp_status lp_last_stats(lp_stats* out);
+
+/* Enable (1) or disable (0) device timing of the phases in lp_stats (CUDA
+ * events on the graph's stream).  Process-wide; off by default. */
+void lp_set_timing(int enable);
+
+/* The CUDA stream (cudaStream_t) the graph's calls run on. */
+void* lp_graph_stream(const lp_graph* g);
+
+/* Thread-local message for the last failing call ("" if none). */
+const char* lp_last_error(void);
+
+/* Library version string. */
+const char* lp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LP_H */

@@ -1,0 +1,280 @@
+"""Python binding of liblp (GPU neighbourhood-based link prediction, sm_103a).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``liblp.so`` built from ``csrc/`` (see ``_build.py``).  The names
+mirror the C ABI in ``include/lp.h``.  There is no CPU fallback: importing
+this package fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblp.so")
+
+MEASURES = ["CN", "JC", "SI", "SC", "HP", "HD", "LHN", "AA", "RA"]
+LP_CN, LP_JC, LP_SI, LP_SC, LP_HP, LP_HD, LP_LHN, LP_AA, LP_RA = range(9)
+LP_CAP_NONE = -1
+LP_MAX_TOPK_PER_SOURCE = 64
+LP_VALIDATE_FULL = 1
+
+STATUS = {0: "LP_OK", 1: "LP_EINVAL", 2: "LP_ENOMEM", 3: "LP_ECUDA", 4: "LP_ETRUNC",
+          5: "LP_ETIMEOUT", 6: "LP_EBUSY", 7: "LP_EINTERNAL"}
+LP_OK, LP_EINVAL, LP_ENOMEM, LP_ECUDA, LP_ETRUNC, LP_ETIMEOUT, LP_EBUSY, LP_EINTERNAL = range(8)
+
+LINK_DTYPE = np.dtype([("u", np.int32), ("v", np.int32), ("score", np.float32),
+                       ("cn", np.int32)])
+
+
+class LPError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class lp_stats(ctypes.Structure):
+    _fields_ = [("wedges", ctypes.c_int64), ("kept_arcs", ctypes.c_int64),
+                ("scanned_arcs", ctypes.c_int64), ("candidates", ctypes.c_int64),
+                ("admitted", ctypes.c_int64), ("warp_sources", ctypes.c_int32),
+                ("cta_items", ctypes.c_int32), ("dense_items", ctypes.c_int32),
+                ("splits", ctypes.c_int32), ("compactions", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("ms_estimate", ctypes.c_float),
+                ("ms_scan", ctypes.c_float), ("ms_select", ctypes.c_float),
+                ("ms_total", ctypes.c_float), ("tier_wedges", ctypes.c_int64 * 2),
+                ("tier_arcs", ctypes.c_int64 * 2), ("tier_kept", ctypes.c_int64 * 2),
+                ("tier_launches", ctypes.c_int32 * 2), ("tier_ms", ctypes.c_float * 2)]
+
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_vp = ctypes.c_void_p
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"liblp.so is not built ({LIB_PATH}); run "
+                          "paper_2401_11415_gb300._build.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    st = ctypes.c_int
+    lib.lp_graph_create.restype = st
+    lib.lp_graph_create.argtypes = [ctypes.c_int32, _vp, _vp, ctypes.c_uint32,
+                                    ctypes.POINTER(_vp)]
+    lib.lp_graph_destroy.restype = st
+    lib.lp_graph_destroy.argtypes = [_vp]
+    lib.lp_graph_info.restype = st
+    lib.lp_graph_info.argtypes = [_vp, _i32p, ctypes.POINTER(ctypes.c_int64), _i32p]
+    lib.lp_predict.restype = st
+    lib.lp_predict.argtypes = [_vp, ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                               _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    lib.lp_predict_dev.restype = st
+    lib.lp_predict_dev.argtypes = lib.lp_predict.argtypes
+    lib.lp_predict_sources.restype = st
+    lib.lp_predict_sources.argtypes = [_vp, ctypes.c_int, ctypes.c_int32, _vp, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_double, _vp, _vp]
+    lib.lp_predict_sources_dev.restype = st
+    lib.lp_predict_sources_dev.argtypes = lib.lp_predict_sources.argtypes
+    lib.lp_last_stats.restype = st
+    lib.lp_last_stats.argtypes = [ctypes.POINTER(lp_stats)]
+    lib.lp_set_timing.restype = None
+    lib.lp_set_timing.argtypes = [ctypes.c_int]
+    lib.lp_graph_stream.restype = _vp
+    lib.lp_graph_stream.argtypes = [_vp]
+    lib.lp_last_error.restype = ctypes.c_char_p
+    lib.lp_last_error.argtypes = []
+    lib.lp_set_option.restype = st
+    lib.lp_set_option.argtypes = [ctypes.c_int, ctypes.c_int64]
+    lib.lp_get_option.restype = ctypes.c_int64
+    lib.lp_get_option.argtypes = [ctypes.c_int]
+    lib.lp_version.restype = ctypes.c_char_p
+    lib.lp_version.argtypes = []
+    _lib = lib
+    return lib
+
+
+def lib():
+    """The loaded ctypes library."""
+    return _load()
+
+
+def _check(status: int, allow=()):
+    if status != LP_OK and status not in allow:
+        raise LPError(status, lp_last_error())
+    return status
+
+
+def _measure(m) -> int:
+    return MEASURES.index(m.upper()) if isinstance(m, str) else int(m)
+
+
+def _cap(cap) -> int:
+    if cap is None or cap == float("inf") or cap < 0:
+        return LP_CAP_NONE
+    return int(min(cap, 2**31 - 1))
+
+
+def _ptr(x):
+    """Host numpy array or torch tensor (host or device) -> address."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return int(x)
+
+
+# ------------------------------------------------------------ C ABI names --
+
+def lp_last_error() -> str:
+    return _load().lp_last_error().decode()
+
+
+def lp_version() -> str:
+    return _load().lp_version().decode()
+
+
+def lp_set_timing(enable: bool) -> None:
+    _load().lp_set_timing(1 if enable else 0)
+
+
+def lp_graph_create(n: int, offsets, indices, flags: int = 0):
+    off = np.ascontiguousarray(offsets, dtype=np.int32)
+    idx = np.ascontiguousarray(indices, dtype=np.int32)
+    if off.size != n + 1:
+        raise ValueError("offsets must have n + 1 entries")
+    h = _vp()
+    _check(_load().lp_graph_create(n, off.ctypes.data, idx.ctypes.data if idx.size else None,
+                                   flags, ctypes.byref(h)))
+    return h
+
+
+def lp_graph_destroy(h) -> None:
+    if h:
+        _load().lp_graph_destroy(h)
+
+
+def lp_graph_info(h):
+    n = ctypes.c_int32()
+    a = ctypes.c_int64()
+    d = ctypes.c_int32()
+    _check(_load().lp_graph_info(h, ctypes.byref(n), ctypes.byref(a), ctypes.byref(d)))
+    return n.value, a.value, d.value
+
+
+def lp_graph_stream(h) -> int:
+    return _load().lp_graph_stream(h) or 0
+
+
+def lp_predict(h, measure, degree_cap=None, k: int = 0, threshold: float = 0.0,
+               out_cap: int | None = None):
+    """Global mode; returns a numpy array of LINK_DTYPE (host buffers)."""
+    lib = _load()
+    cnt = ctypes.c_int64(0)
+    m, c = _measure(measure), _cap(degree_cap)
+    if out_cap is None:
+        out_cap = k if k > 0 else 0
+    out = np.zeros(max(out_cap, 1), dtype=LINK_DTYPE)
+    st = lib.lp_predict(h, m, c, k, threshold, out.ctypes.data, out_cap, ctypes.byref(cnt))
+    if st == LP_ETRUNC and out_cap == 0 and k == 0:
+        out = np.zeros(max(cnt.value, 1), dtype=LINK_DTYPE)
+        st = lib.lp_predict(h, m, c, k, threshold, out.ctypes.data, cnt.value, ctypes.byref(cnt))
+    _check(st)
+    return out[: cnt.value].copy()
+
+
+def lp_predict_dev(h, measure, degree_cap, k: int, threshold: float, d_out, out_cap: int) -> int:
+    """Global mode into a device buffer (torch tensor or address); returns the
+    number of links found."""
+    cnt = ctypes.c_int64(0)
+    _check(_load().lp_predict_dev(h, _measure(measure), _cap(degree_cap), k, threshold,
+                                  _ptr(d_out), out_cap, ctypes.byref(cnt)))
+    return cnt.value
+
+
+def lp_predict_sources(h, measure, sources, k: int, degree_cap=None, threshold: float = 0.0):
+    """Per-source mode (host buffers); returns (links[n_src, k], counts[n_src])."""
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    ns = src.size
+    out = np.zeros(max(ns * k, 1), dtype=LINK_DTYPE)
+    counts = np.zeros(max(ns, 1), dtype=np.int32)
+    _check(_load().lp_predict_sources(h, _measure(measure), _cap(degree_cap),
+                                      src.ctypes.data if ns else None, ns, k, threshold,
+                                      out.ctypes.data, counts.ctypes.data))
+    return out[: ns * k].reshape(ns, k), counts[:ns].copy()
+
+
+def lp_predict_sources_dev(h, measure, d_sources, n_src: int, k: int, degree_cap, threshold,
+                           d_out, d_counts) -> None:
+    _check(_load().lp_predict_sources_dev(h, _measure(measure), _cap(degree_cap),
+                                          _ptr(d_sources), n_src, k, threshold, _ptr(d_out),
+                                          _ptr(d_counts)))
+
+
+LP_OPT_SELECT_BUFFER, LP_OPT_WARP_MAX_WEDGES, LP_OPT_CTA_MAX_WEDGES, LP_OPT_SPLIT_TARGET, \
+    LP_OPT_SPLIT_LOGCAP = range(1, 6)
+
+
+def lp_set_option(option: int, value: int) -> None:
+    _check(_load().lp_set_option(option, value))
+
+
+def lp_get_option(option: int) -> int:
+    return int(_load().lp_get_option(option))
+
+
+def lp_last_stats() -> dict:
+    s = lp_stats()
+    _check(_load().lp_last_stats(ctypes.byref(s)))
+    out = {}
+    for f, _ in lp_stats._fields_:
+        v = getattr(s, f)
+        out[f] = list(v) if hasattr(v, "__len__") else v
+    return out
+
+
+class Graph:
+    """Owning wrapper of an lp_graph handle."""
+
+    def __init__(self, n, offsets, indices, flags: int = 0):
+        self.n = int(n)
+        self.handle = lp_graph_create(self.n, offsets, indices, flags)
+
+    @classmethod
+    def from_csr(cls, g, flags: int = 0):
+        return cls(g.n, g.off, g.idx, flags)
+
+    def info(self):
+        return lp_graph_info(self.handle)
+
+    def predict(self, measure, degree_cap=None, k=0, threshold=0.0):
+        return lp_predict(self.handle, measure, degree_cap, k, threshold)
+
+    def predict_sources(self, measure, sources, k, degree_cap=None, threshold=0.0):
+        return lp_predict_sources(self.handle, measure, sources, k, degree_cap, threshold)
+
+    @property
+    def stream(self) -> int:
+        return lp_graph_stream(self.handle)
+
+    def close(self):
+        if self.handle:
+            lp_graph_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,897 @@
+// lp_api.cu -- the C ABI of liblp: graph residency and the predict calls.
+//
+// Graph residency: the CSR is validated on the host, uploaded once, and a
+// per-arc table is built on the device (for arc a -> b: the position of a in
+// the sorted list of b, the end of that list and |Gamma_b|), so that the scan
+// finds the c > a suffix of Gamma_b without searching and tests the hub limit
+// without touching Gamma_b (Algorithm 1; Sections 4.1.2 and 4.2.1).
+//
+// Global mode (Algorithm 1 end to end): estimate and bin the sources, scan
+// them, and select the N_P best pairs.  The paper keeps a top-N_P heap per
+// thread and merges the heaps sequentially (Section 4.1.7).  Here every
+// scored pair that ranks before a running threshold T is appended to one
+// device buffer; when the buffer fills, it is sorted exactly, cut to N_P,
+// and T becomes its N_P-th entry, so later pairs must beat it.  Work that
+// was in flight when the buffer filled is re-queued and its partial output
+// removed, which keeps the result exact and deterministic.
+#include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "lp_internal.cuh"
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+using namespace lp;
+
+struct lp_graph : public lp::Graph {};
+
+namespace lp {
+
+static thread_local std::string t_err;
+static thread_local lp_stats t_stats;
+static std::atomic<int> g_timing{0};
+static std::mutex g_opt_mu;
+static Options g_opt;
+
+Options options_snapshot() {
+  std::lock_guard<std::mutex> l(g_opt_mu);
+  return g_opt;
+}
+
+static lp_status fail(lp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return s;
+}
+
+static lp_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky-free error
+  return fail(e == cudaErrorMemoryAllocation ? LP_ENOMEM : LP_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define CU(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
+  } while (0)
+
+// Grow a scratch allocation to at least `bytes` (contents are not kept).
+static cudaError_t ensure(Graph& g, Graph::Scratch& s, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (s.bytes >= bytes) return cudaSuccess;
+  if (s.p) {
+    cudaStreamSynchronize(g.stream);
+    cudaFree(s.p);
+    s.p = nullptr;
+    s.bytes = 0;
+  }
+  size_t want = bytes + bytes / 4;
+  cudaError_t e = cudaMalloc(&s.p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&s.p, bytes);
+    if (e != cudaSuccess) return e;
+    want = bytes;
+  }
+  s.bytes = want;
+  return cudaSuccess;
+}
+
+template <typename T>
+static T* sp(Graph::Scratch& s) {
+  return reinterpret_cast<T*>(s.p);
+}
+
+// ------------------------------------------------------ graph residency --
+
+// One warp per vertex a: deg[a] and the arc table of a's arcs; sets *err if
+// some reverse arc is missing.
+__global__ void k_build_arcs(const int* __restrict__ off, const int* __restrict__ idx, int n,
+                             int* __restrict__ deg, Arc* __restrict__ arc, int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int a = warp; a < n; a += nwarps) {
+    const int e0 = off[a], e1 = off[a + 1];
+    if (lane == 0) deg[a] = e1 - e0;
+    for (int e = e0 + lane; e < e1; e += 32) {
+      const int b = idx[e];
+      int l = off[b], r = off[b + 1];
+      const int end = r;
+      while (l < r) {
+        const int m = (l + r) >> 1;
+        if (idx[m] < a) l = m + 1; else r = m;
+      }
+      if (l >= end || idx[l] != a) {
+        atomicExch(err, 1);
+        l = end - 1;
+      }
+      arc[e] = make_int4(l, end, end - off[b], b);
+    }
+  }
+}
+
+static void free_graph(Graph* g) {
+  if (!g) return;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  Graph::Scratch* all[] = {&g->s_ctr, &g->s_w, &g->s_warpq, &g->s_itemq, &g->s_warpq2,
+                           &g->s_itemq2, &g->s_buf, &g->s_buf2, &g->s_failed, &g->s_split,
+                           &g->s_thresh, &g->s_flags, &g->s_partial, &g->s_phdr, &g->s_top,
+                           &g->s_cnt, &g->s_links, &g->s_src, &g->s_grp};
+  for (auto* s : all)
+    if (s->p) cudaFree(s->p);
+  cudaFree(g->d_off);
+  cudaFree(g->d_idx);
+  cudaFree(g->d_deg);
+  cudaFree(g->d_arc);
+  for (auto& e : g->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : g->kev)
+    if (e) cudaEventDestroy(e);
+  if (g->stream) cudaStreamDestroy(g->stream);
+  delete static_cast<lp_graph*>(g);
+}
+
+}  // namespace lp
+
+extern "C" {
+
+const char* lp_last_error(void) { return lp::t_err.c_str(); }
+
+const char* lp_version(void) { return "liblp 0.1 (sm_103a)"; }
+
+void lp_set_timing(int enable) { lp::g_timing.store(enable ? 1 : 0); }
+
+lp_status lp_set_option(lp_option option, int64_t value) {
+  std::lock_guard<std::mutex> l(lp::g_opt_mu);
+  switch (option) {
+    case LP_OPT_SELECT_BUFFER:
+      if (value < 16 || value > (1ll << 34)) break;
+      lp::g_opt.select_buffer = value;
+      return LP_OK;
+    case LP_OPT_WARP_MAX_WEDGES:
+      if (value < 1 || value > lp::kWarpMaxWedges) break;
+      lp::g_opt.warp_max = (int)value;
+      return LP_OK;
+    case LP_OPT_CTA_MAX_WEDGES:
+      if (value < 513 || value > lp::kCtaMaxWedges) break;
+      lp::g_opt.cta_max = (int)value;
+      return LP_OK;
+    case LP_OPT_SPLIT_TARGET:
+      if (value < 256 || value > 12288) break;
+      lp::g_opt.split_target = (int)value;
+      return LP_OK;
+    case LP_OPT_SPLIT_LOGCAP:
+      if (value < 6 || value > 14) break;
+      lp::g_opt.split_logcap = (int)value;
+      return LP_OK;
+    default:
+      break;
+  }
+  return fail(LP_EINVAL, "lp_set_option: option %d value %lld out of range", (int)option,
+              (long long)value);
+}
+
+int64_t lp_get_option(lp_option option) {
+  const lp::Options o = lp::options_snapshot();
+  switch (option) {
+    case LP_OPT_SELECT_BUFFER: return o.select_buffer;
+    case LP_OPT_WARP_MAX_WEDGES: return o.warp_max;
+    case LP_OPT_CTA_MAX_WEDGES: return o.cta_max;
+    case LP_OPT_SPLIT_TARGET: return o.split_target;
+    case LP_OPT_SPLIT_LOGCAP: return o.split_logcap;
+    default: return -1;
+  }
+}
+
+lp_status lp_last_stats(lp_stats* out) {
+  if (!out) return fail(LP_EINVAL, "lp_last_stats: null output");
+  *out = lp::t_stats;
+  return LP_OK;
+}
+
+void* lp_graph_stream(const lp_graph* g) { return g ? (void*)g->stream : nullptr; }
+
+lp_status lp_graph_info(const lp_graph* g, int32_t* n, int64_t* arcs, int32_t* max_degree) {
+  if (!g) return fail(LP_EINVAL, "lp_graph_info: null graph");
+  if (n) *n = g->n;
+  if (arcs) *arcs = g->arcs;
+  if (max_degree) *max_degree = g->dmax;
+  return LP_OK;
+}
+
+lp_status lp_graph_destroy(lp_graph* g) {
+  lp::free_graph(g);
+  return LP_OK;
+}
+
+lp_status lp_graph_create(int32_t n, const int32_t* offsets, const int32_t* indices,
+                          uint32_t flags, lp_graph** out) {
+  if (!out) return fail(LP_EINVAL, "lp_graph_create: null output handle");
+  *out = nullptr;
+  if (n < 0) return fail(LP_EINVAL, "lp_graph_create: n < 0");
+  if (!offsets) return fail(LP_EINVAL, "lp_graph_create: null offsets");
+  if (offsets[0] != 0) return fail(LP_EINVAL, "lp_graph_create: offsets[0] != 0");
+  for (int32_t v = 0; v < n; ++v)
+    if (offsets[v + 1] < offsets[v])
+      return fail(LP_EINVAL, "lp_graph_create: offsets decrease at vertex %d", v);
+  const int64_t A = offsets[n];
+  if (A < 0 || A >= INT32_MAX) return fail(LP_EINVAL, "lp_graph_create: too many arcs");
+  if (A > 0 && !indices) return fail(LP_EINVAL, "lp_graph_create: null indices");
+  // range, self-loops, order
+  int bad_range = 0, bad_loop = 0, unsorted = 0, dup = 0;
+  int32_t dmax = 0;
+#pragma omp parallel for schedule(dynamic, 4096) reduction(| : bad_range, bad_loop, unsorted, dup) reduction(max : dmax)
+  for (int32_t v = 0; v < n; ++v) {
+    const int32_t d = offsets[v + 1] - offsets[v];
+    if (d > dmax) dmax = d;
+    for (int32_t e = offsets[v]; e < offsets[v + 1]; ++e) {
+      const int32_t x = indices[e];
+      if (x < 0 || x >= n) bad_range = 1;
+      if (x == v) bad_loop = 1;
+      if (e > offsets[v]) {
+        if (indices[e - 1] > x) unsorted = 1;
+        else if (indices[e - 1] == x) dup = 1;
+      }
+    }
+  }
+  if (bad_range) return fail(LP_EINVAL, "lp_graph_create: neighbour index out of range");
+  if (bad_loop) return fail(LP_EINVAL, "lp_graph_create: self-loop");
+  std::vector<int32_t> sorted;
+  const int32_t* idx = indices;
+  if (unsorted) {
+    sorted.assign(indices, indices + A);
+    dup = 0;
+#pragma omp parallel for schedule(dynamic, 1024) reduction(| : dup)
+    for (int32_t v = 0; v < n; ++v) {
+      std::sort(sorted.begin() + offsets[v], sorted.begin() + offsets[v + 1]);
+      for (int32_t e = offsets[v] + 1; e < offsets[v + 1]; ++e)
+        if (sorted[e] == sorted[e - 1]) dup = 1;
+    }
+    idx = sorted.data();
+  }
+  if (dup) return fail(LP_EINVAL, "lp_graph_create: duplicate arc");
+  if (flags & LP_VALIDATE_FULL) {
+    int asym = 0;
+#pragma omp parallel for schedule(dynamic, 1024) reduction(| : asym)
+    for (int32_t v = 0; v < n; ++v)
+      for (int32_t e = offsets[v]; e < offsets[v + 1]; ++e) {
+        const int32_t b = idx[e];
+        if (!std::binary_search(idx + offsets[b], idx + offsets[b + 1], v)) asym = 1;
+      }
+    if (asym) return fail(LP_EINVAL, "lp_graph_create: missing reverse arc");
+  }
+
+  lp_graph* g = new (std::nothrow) lp_graph();
+  if (!g) return fail(LP_ENOMEM, "lp_graph_create: host allocation");
+  g->n = n;
+  g->arcs = A;
+  g->dmax = dmax;
+  {
+    int lg = 0;
+    while ((1ll << lg) < (int64_t)dmax + 1) ++lg;
+    int f = 62 - lg;
+    g->fixbits = f > 50 ? 50 : (f < 8 ? 8 : f);
+  }
+  cudaError_t e = cudaGetDevice(&g->device);
+  int* d_err = nullptr;
+  int h_err = 0;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_off, sizeof(int) * ((size_t)n + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_idx, sizeof(int) * (size_t)(A > 0 ? A : 1));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_deg, sizeof(int) * (size_t)(n > 0 ? n : 1));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_arc, sizeof(Arc) * (size_t)(A > 0 ? A : 1));
+  if (e == cudaSuccess) e = cudaMalloc(&d_err, sizeof(int));
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->ev[i]);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->kev[i]);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->d_off, offsets, sizeof(int) * ((size_t)n + 1), cudaMemcpyHostToDevice,
+                        g->stream);
+  if (e == cudaSuccess && A > 0)
+    e = cudaMemcpyAsync(g->d_idx, idx, sizeof(int) * (size_t)A, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), g->stream);
+  if (e == cudaSuccess && n > 0) {
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>(((int64_t)n * 32 + threads - 1) / threads, 152 * 16);
+    k_build_arcs<<<blocks, threads, 0, g->stream>>>(g->d_off, g->d_idx, n, g->d_deg, g->d_arc,
+                                                    d_err);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (d_err) cudaFree(d_err);
+  if (e != cudaSuccess) {
+    lp_status s = cuda_fail(e, "lp_graph_create");
+    free_graph(g);
+    return s;
+  }
+  if (h_err) {
+    free_graph(g);
+    return fail(LP_EINVAL, "lp_graph_create: missing reverse arc (graph is not undirected)");
+  }
+  *out = g;
+  return LP_OK;
+}
+
+}  // extern "C"
+
+namespace lp {
+
+// ------------------------------------------------------------ utilities --
+
+static void begin_stats() {
+  memset(&t_stats, 0, sizeof(t_stats));
+  t_err.clear();
+}
+
+struct Timer {
+  Graph& g;
+  bool on;
+  explicit Timer(Graph& gg) : g(gg), on(g_timing.load() != 0) {}
+  void mark(int i) {
+    if (on) cudaEventRecord(g.ev[i], g.stream);
+  }
+  float ms(int i, int j) {
+    if (!on) return 0.f;
+    float t = 0.f;
+    cudaEventSynchronize(g.ev[j]);
+    cudaEventElapsedTime(&t, g.ev[i], g.ev[j]);
+    return t;
+  }
+};
+
+// Launch both scan kernels; with timing on, time each on the graph's stream.
+static cudaError_t scan_launches(Graph& g, const ScanArgs& A, const int4* wq, u64 nw,
+                                 const int4* cq, u64 nc, bool timing) {
+  cudaStream_t st = g.stream;
+  if (timing && nw) cudaEventRecord(g.kev[0], st);
+  cudaError_t e = launch_scan_warp(A, wq, nw, st);
+  if (e != cudaSuccess) return e;
+  if (timing && nw) cudaEventRecord(g.kev[1], st);
+  if (timing && nc) cudaEventRecord(g.kev[2], st);
+  e = launch_scan_cta(A, cq, nc, st);
+  if (e != cudaSuccess) return e;
+  if (timing && nc) cudaEventRecord(g.kev[3], st);
+  if (nw) t_stats.tier_launches[0]++;
+  if (nc) t_stats.tier_launches[1]++;
+  return cudaSuccess;
+}
+
+// After the stream synchronised: add the kernels' event times to the stats.
+static void scan_times(Graph& g, u64 nw, u64 nc, bool timing) {
+  if (!timing) return;
+  float t = 0.f;
+  if (nw && cudaEventElapsedTime(&t, g.kev[0], g.kev[1]) == cudaSuccess) t_stats.tier_ms[0] += t;
+  if (nc && cudaEventElapsedTime(&t, g.kev[2], g.kev[3]) == cudaSuccess) t_stats.tier_ms[1] += t;
+}
+
+static void estimate_stats(const Counters& h) {
+  t_stats.wedges = (int64_t)h.wedges;
+  t_stats.kept_arcs = (int64_t)h.kept_arcs;
+  t_stats.scanned_arcs = (int64_t)h.scanned_arcs;
+  t_stats.warp_sources = (int32_t)h.nwarp;
+  t_stats.cta_items = (int32_t)h.nitem;
+  t_stats.dense_items = (int32_t)h.dense_items;
+  for (int i = 0; i < 2; ++i) {
+    t_stats.tier_wedges[i] = (int64_t)h.tier_wedges[i];
+    t_stats.tier_arcs[i] = (int64_t)h.tier_arcs[i];
+    t_stats.tier_kept[i] = (int64_t)h.tier_kept[i];
+  }
+}
+
+static ScanArgs base_args(Graph& g, int measure, int cap, double threshold, int mode) {
+  ScanArgs A;
+  memset(&A, 0, sizeof(A));
+  const Options o = options_snapshot();
+  A.warp_max = o.warp_max;
+  A.cta_max = o.cta_max;
+  A.split_target = o.split_target;
+  A.split_logcap = o.split_logcap;
+  A.off = g.d_off;
+  A.idx = g.d_idx;
+  A.deg = g.d_deg;
+  A.arc = g.d_arc;
+  A.n = g.n;
+  A.cap = cap < 0 ? INT32_MAX : cap;
+  A.measure = measure;
+  A.mode = mode;
+  A.fixbits = g.fixbits;
+  A.thr_check = (threshold <= 0.0) ? 0 : 1;  // scores are > 0; NaN keeps the test
+  A.threshold = threshold;
+  return A;
+}
+
+// Split an overflowed hash item into two halves (dense when narrow enough).
+static void split_item(const int4& r, int dense_span, std::vector<int4>& out) {
+  const int lo = r.y, hi = r.z;
+  const int logcap = (r.w >> 8) & 0xff;
+  if (hi - lo <= dense_span) {
+    out.push_back(make_int4(r.x, lo, hi, kItemDense | (logcap << 8)));
+    return;
+  }
+  const int mid = lo + (hi - lo) / 2;
+  out.push_back(make_int4(r.x, lo, mid, (logcap << 8)));
+  out.push_back(make_int4(r.x, mid, hi, (logcap << 8)));
+}
+
+// Queue = host records followed by a device remainder [src + from, src + to).
+static cudaError_t build_queue(Graph& g, Graph::Scratch& dst, const std::vector<int4>& head,
+                               const int4* src, u64 from, u64 to, u64* len) {
+  const u64 rem = to > from ? to - from : 0;
+  const u64 total = head.size() + rem;
+  *len = total;
+  cudaError_t e = ensure(g, dst, sizeof(int4) * (total + 1));
+  if (e != cudaSuccess) return e;
+  if (!head.empty())
+    e = cudaMemcpyAsync(dst.p, head.data(), sizeof(int4) * head.size(), cudaMemcpyHostToDevice,
+                        g.stream);
+  if (e == cudaSuccess && rem)
+    e = cudaMemcpyAsync(sp<int4>(dst) + head.size(), src + from, sizeof(int4) * rem,
+                        cudaMemcpyDeviceToDevice, g.stream);
+  if (e == cudaSuccess && !head.empty()) e = cudaStreamSynchronize(g.stream);  // head is stack data
+  return e;
+}
+
+__global__ void k_set_flags(const int4* __restrict__ rec, int n, unsigned char* __restrict__ flag,
+                            unsigned char v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[rec[i].x] = v;
+}
+
+__global__ void k_check_sources(const int* __restrict__ s, int n_src, int n, int* __restrict__ bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_src && (s[i] < 0 || s[i] >= n)) atomicExch(bad, 1);
+}
+
+// ---------------------------------------------------------- global mode --
+
+static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, double threshold,
+                                lp_link* out, bool out_dev, int64_t out_cap, int64_t* out_n) {
+  begin_stats();
+  *out_n = 0;
+  if (measure < 0 || measure > LP_RA) return fail(LP_EINVAL, "lp_predict: bad measure");
+  if (k < 0) return fail(LP_EINVAL, "lp_predict: k < 0");
+  if (out_cap < 0 || (out_cap > 0 && !out)) return fail(LP_EINVAL, "lp_predict: bad output buffer");
+  if (g.n == 0 || cap == 0) return LP_OK;
+  std::lock_guard<std::mutex> lock(g.mu);
+  CU(cudaSetDevice(g.device));
+  cudaStream_t st = g.stream;
+  Timer tm(g);
+  tm.mark(0);
+  ScanArgs A = base_args(g, measure, cap, threshold, 0);
+  const int dense_span = (measure == LP_AA || measure == LP_RA) ? kCtaSmem / 8 : kCtaSmem / 4;
+  // selection buffer
+  const u64 minbuf = (u64)std::max<long long>(16, options_snapshot().select_buffer);
+  u64 C = k > 0 ? std::max<u64>(minbuf, 2ull * (u64)k + std::min<u64>(minbuf, 1ull << 20)) : minbuf;
+  const u64 failed_cap = 1 << 20, split_cap = 1 << 20;
+  CU(ensure(g, g.s_ctr, sizeof(Counters)));
+  CU(ensure(g, g.s_thresh, sizeof(Thresh)));
+  CU(ensure(g, g.s_warpq, sizeof(int4) * ((size_t)g.n + 1)));
+  CU(ensure(g, g.s_buf, sizeof(Cand) * C));
+  CU(ensure(g, g.s_buf2, sizeof(Cand) * C));
+  CU(ensure(g, g.s_failed, sizeof(int4) * failed_cap));
+  CU(ensure(g, g.s_split, sizeof(int4) * split_cap));
+  CU(ensure(g, g.s_flags, (size_t)g.n + 1));
+  CU(ensure(g, g.s_grp, sizeof(int) * sort_splits_needed(C)));
+  u64 itemq_cap = std::max<u64>(1024, g.s_itemq.bytes / sizeof(int4));
+  CU(ensure(g, g.s_itemq, sizeof(int4) * itemq_cap));
+  Counters* d_ctr = sp<Counters>(g.s_ctr);
+  Thresh* d_th = sp<Thresh>(g.s_thresh);
+  CU(cudaMemsetAsync(d_th, 0, sizeof(Thresh), st));
+  CU(cudaMemsetAsync(g.s_flags.p, 0, (size_t)g.n + 1, st));
+  Counters h{};
+  // estimate + binning (re-run if the item queue was too small)
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    CU(cudaMemsetAsync(d_ctr, 0, sizeof(Counters), st));
+    A.ctr = d_ctr;
+    CU(launch_estimate(A, g.n, sp<int4>(g.s_warpq), sp<int4>(g.s_itemq), itemq_cap, nullptr, st));
+    t_stats.launches++;
+    CU(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (h.nitem <= itemq_cap) break;
+    itemq_cap = h.nitem + 1024;
+    CU(ensure(g, g.s_itemq, sizeof(int4) * itemq_cap));
+  }
+  if (h.nitem > itemq_cap) return fail(LP_EINTERNAL, "lp_predict: item queue sizing");
+  estimate_stats(h);
+  tm.mark(1);
+
+  // queues: current lists live in s_warpq / s_itemq; rebuilt lists go to the
+  // *2 buffers and are swapped in
+  Graph::Scratch* wq = &g.s_warpq;
+  Graph::Scratch* wq2 = &g.s_warpq2;
+  Graph::Scratch* cq = &g.s_itemq;
+  Graph::Scratch* cq2 = &g.s_itemq2;
+  u64 nw = h.nwarp, nc = h.nitem;
+  u64 kept = 0;  // valid entries at the start of the buffer
+  std::vector<int4> failed, splits, headw, headc;
+  for (int round = 0; nw + nc > 0; ++round) {
+    if (round > 100000) return fail(LP_EINTERNAL, "lp_predict: no progress");
+    // reset the per-launch counters, keep the buffer fill
+    Counters z{};
+    z.cand_cnt = kept;
+    CU(cudaMemcpyAsync(d_ctr, &z, sizeof(Counters), cudaMemcpyHostToDevice, st));
+    A.ctr = d_ctr;
+    A.buf = sp<Cand>(g.s_buf);
+    A.buf_cap = C;
+    A.thresh = d_th;
+    A.failed = sp<int4>(g.s_failed);
+    A.failed_cap = failed_cap;
+    A.split = sp<int4>(g.s_split);
+    A.split_cap = split_cap;
+    CU(scan_launches(g, A, sp<int4>(*wq), nw, sp<int4>(*cq), nc, tm.on));
+    t_stats.launches += (nw > 0) + (nc > 0);
+    CU(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    scan_times(g, nw, nc, tm.on);
+    if (h.error) return fail(LP_EINTERNAL, "lp_predict: device check %u", h.error);
+    t_stats.candidates += (int64_t)h.candidates;
+    failed.resize(h.nfailed);
+    splits.resize(h.nsplit);
+    if (h.nfailed)
+      CU(cudaMemcpy(failed.data(), g.s_failed.p, sizeof(int4) * h.nfailed, cudaMemcpyDeviceToHost));
+    if (h.nsplit)
+      CU(cudaMemcpy(splits.data(), g.s_split.p, sizeof(int4) * h.nsplit, cudaMemcpyDeviceToHost));
+    const u64 done_w = std::min<u64>(h.claim_w, nw), done_c = std::min<u64>(h.claim_c, nc);
+    u64 valid = std::min<u64>(h.cand_cnt, C);
+    t_stats.splits += (int32_t)h.nsplit;
+    if (h.full) {
+      // compaction: drop failed output, then sort and cut to k
+      t_stats.compactions++;
+      Cand* src = sp<Cand>(g.s_buf);
+      u64 m = valid;
+      if (!failed.empty()) {
+        std::vector<int4> fs(failed);
+        std::sort(fs.begin(), fs.end(), [](const int4& x, const int4& y) {
+          return x.x != y.x ? x.x < y.x : x.y < y.y;
+        });
+        CU(cudaMemcpyAsync(g.s_split.p, fs.data(), sizeof(int4) * fs.size(), cudaMemcpyHostToDevice,
+                           st));
+        const int nf = (int)fs.size();
+        k_set_flags<<<(nf + 255) / 256, 256, 0, st>>>(sp<int4>(g.s_split), nf,
+                                                      sp<unsigned char>(g.s_flags), 1);
+        u64* d_cnt = &d_ctr->pad[0];
+        CU(cudaMemsetAsync(d_cnt, 0, sizeof(u64), st));
+        CU(launch_filter_failed(src, valid, sp<unsigned char>(g.s_flags), sp<int4>(g.s_split), nf,
+                                sp<Cand>(g.s_buf2), d_ctr, d_cnt, st));
+        k_set_flags<<<(nf + 255) / 256, 256, 0, st>>>(sp<int4>(g.s_split), nf,
+                                                      sp<unsigned char>(g.s_flags), 0);
+        t_stats.launches += 3;
+        CU(cudaMemcpyAsync(&m, d_cnt, sizeof(u64), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        std::swap(g.s_buf, g.s_buf2);
+        src = sp<Cand>(g.s_buf);
+      }
+      if (k > 0) {
+        Cand* res = nullptr;
+        CU(launch_sort_cands(src, sp<Cand>(g.s_buf2), sp<int>(g.s_grp), m, st, &res,
+                             &t_stats.launches));
+        const u64 keepn = std::min<u64>(m, (u64)k);
+        if (res != src) CU(cudaMemcpyAsync(src, res, sizeof(Cand) * keepn, cudaMemcpyDeviceToDevice, st));
+        if (m >= (u64)k) {
+          CU(launch_set_thresh(src, (u64)k, d_th, st));
+          t_stats.launches++;
+        }
+        kept = keepn;
+      } else {
+        kept = m;
+      }
+      // guarantee room for progress
+      const bool progress = (done_w + done_c) > h.nfailed;
+      if (k == 0 || !progress || C - kept < (C >> 2)) {
+        const u64 C2 = C * 2;
+        CU(ensure(g, g.s_buf2, sizeof(Cand) * C2));
+        CU(cudaMemcpyAsync(g.s_buf2.p, g.s_buf.p, sizeof(Cand) * kept, cudaMemcpyDeviceToDevice, st));
+        CU(cudaStreamSynchronize(st));
+        std::swap(g.s_buf, g.s_buf2);
+        CU(ensure(g, g.s_buf2, sizeof(Cand) * C2));
+        CU(ensure(g, g.s_grp, sizeof(int) * sort_splits_needed(C2)));
+        C = C2;
+      }
+    } else {
+      kept = valid;
+    }
+    // next queues: failed records, split halves, then what was never claimed
+    headw.clear();
+    headc.clear();
+    for (const int4& r : failed) {
+      if (r.w & (1 << 30)) headw.push_back(r);
+      else headc.push_back(r);
+    }
+    for (const int4& r : splits) split_item(r, dense_span, headc);
+    u64 nw2 = 0, nc2 = 0;
+    CU(build_queue(g, *wq2, headw, sp<int4>(*wq), done_w, nw, &nw2));
+    CU(build_queue(g, *cq2, headc, sp<int4>(*cq), done_c, nc, &nc2));
+    std::swap(wq, wq2);
+    std::swap(cq, cq2);
+    nw = nw2;
+    nc = nc2;
+  }
+  tm.mark(2);
+  // final selection
+  Cand* src = sp<Cand>(g.s_buf);
+  Cand* res = src;
+  CU(launch_sort_cands(src, sp<Cand>(g.s_buf2), sp<int>(g.s_grp), kept, st, &res,
+                       &t_stats.launches));
+  const u64 found = k > 0 ? std::min<u64>(kept, (u64)k) : kept;
+  *out_n = (int64_t)found;
+  t_stats.admitted = (int64_t)kept;
+  const u64 nwrite = std::min<u64>(found, (u64)out_cap);
+  lp_link* d_links = nullptr;
+  if (out_dev) {
+    d_links = out;
+  } else {
+    CU(ensure(g, g.s_links, sizeof(lp_link) * (nwrite + 1)));
+    d_links = sp<lp_link>(g.s_links);
+  }
+  if (nwrite) {
+    CU(launch_emit_global(res, nwrite, measure, g.fixbits, d_links, st));
+    t_stats.launches++;
+    if (measure == LP_AA || measure == LP_RA) {
+      CU(launch_pair_cn(d_links, nullptr, 1, nwrite, g.d_off, g.d_idx, g.d_deg, A.cap, st));
+      t_stats.launches++;
+    }
+    if (!out_dev)
+      CU(cudaMemcpyAsync(out, d_links, sizeof(lp_link) * nwrite, cudaMemcpyDeviceToHost, st));
+  }
+  tm.mark(3);
+  CU(cudaStreamSynchronize(st));
+  t_stats.ms_estimate = tm.ms(0, 1);
+  t_stats.ms_scan = tm.ms(1, 2);
+  t_stats.ms_select = tm.ms(2, 3);
+  t_stats.ms_total = tm.ms(0, 3);
+  if (found > (u64)out_cap)
+    return fail(LP_ETRUNC, "lp_predict: %lld links found, room for %lld", (long long)found,
+                (long long)out_cap);
+  return LP_OK;
+}
+
+// ------------------------------------------------------- per-source mode --
+
+static lp_status predict_sources(Graph& g, int measure, int cap, const int* d_src, int n_src, int k,
+                                 double threshold, lp_link* d_out, int* d_counts) {
+  if (n_src == 0) return LP_OK;
+  cudaStream_t st = g.stream;
+  Timer tm(g);
+  tm.mark(0);
+  // reject out-of-range sources before any kernel reads them
+  CU(ensure(g, g.s_ctr, sizeof(Counters)));
+  Counters* d_ctr = sp<Counters>(g.s_ctr);
+  {
+    int* d_bad = reinterpret_cast<int*>(&d_ctr->error);
+    int bad = 0;
+    CU(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+    k_check_sources<<<(n_src + 255) / 256, 256, 0, st>>>(d_src, n_src, g.n, d_bad);
+    CU(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (bad) return fail(LP_EINVAL, "lp_predict_sources: source id out of range");
+  }
+  const int32_t zero = 0;
+  (void)zero;
+  CU(cudaMemsetAsync(d_counts, 0, sizeof(int) * (size_t)n_src, st));
+  if (cap == 0 || g.n == 0) {
+    CU(cudaStreamSynchronize(st));
+    return LP_OK;
+  }
+  ScanArgs A = base_args(g, measure, cap, threshold, 1);
+  const int dense_span = (measure == LP_AA || measure == LP_RA) ? kCtaSmem / 8 : kCtaSmem / 4;
+  A.sources = d_src;
+  A.k = k;
+  CU(ensure(g, g.s_warpq, sizeof(int4) * ((size_t)n_src + 1)));
+  CU(ensure(g, g.s_top, sizeof(TopEnt) * (size_t)n_src * k));
+  CU(ensure(g, g.s_grp, sizeof(int2) * ((size_t)n_src + 1)));
+  CU(ensure(g, g.s_split, sizeof(int4) * (1 << 20)));
+  u64 itemq_cap = std::max<u64>(1024, g.s_itemq.bytes / sizeof(int4));
+  CU(ensure(g, g.s_itemq, sizeof(int4) * itemq_cap));
+  A.out_top = sp<TopEnt>(g.s_top);
+  A.out_cnt = d_counts;
+  Counters h{};
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    CU(cudaMemsetAsync(d_ctr, 0, sizeof(Counters), st));
+    A.ctr = d_ctr;
+    CU(launch_estimate(A, n_src, sp<int4>(g.s_warpq), sp<int4>(g.s_itemq), itemq_cap,
+                       sp<int2>(g.s_grp), st));
+    t_stats.launches++;
+    CU(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (h.nitem <= itemq_cap) break;
+    itemq_cap = h.nitem + 1024;
+    CU(ensure(g, g.s_itemq, sizeof(int4) * itemq_cap));
+  }
+  if (h.nitem > itemq_cap) return fail(LP_EINTERNAL, "lp_predict_sources: item queue sizing");
+  estimate_stats(h);
+  tm.mark(1);
+  // partial lists: one per non-single item, including split halves
+  u64 partial_cap = h.nitem + 16;
+  CU(ensure(g, g.s_partial, sizeof(TopEnt) * partial_cap * k));
+  CU(ensure(g, g.s_phdr, sizeof(int2) * partial_cap));
+  Graph::Scratch* cq = &g.s_itemq;
+  Graph::Scratch* cq2 = &g.s_itemq2;
+  u64 nw = h.nwarp, nc = h.nitem;
+  u64 npartial = 0;
+  std::vector<int4> splits, headc;
+  const std::vector<int4> none;
+  for (int round = 0; nw + nc > 0; ++round) {
+    if (round > 10000) return fail(LP_EINTERNAL, "lp_predict_sources: no progress");
+    Counters z{};
+    z.npartial = npartial;
+    CU(cudaMemcpyAsync(d_ctr, &z, sizeof(Counters), cudaMemcpyHostToDevice, st));
+    A.ctr = d_ctr;
+    A.split = sp<int4>(g.s_split);
+    A.split_cap = 1 << 20;
+    A.partial = sp<TopEnt>(g.s_partial);
+    A.partial_hdr = sp<int2>(g.s_phdr);
+    A.partial_cap = partial_cap;
+    CU(scan_launches(g, A, sp<int4>(g.s_warpq), nw, sp<int4>(*cq), nc, tm.on));
+    t_stats.launches += (nw > 0) + (nc > 0);
+    CU(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    scan_times(g, nw, nc, tm.on);
+    if (h.error) return fail(LP_EINTERNAL, "lp_predict_sources: device check %u", h.error);
+    t_stats.candidates += (int64_t)h.candidates;
+    t_stats.splits += (int32_t)h.nsplit;
+    npartial = h.npartial;
+    splits.resize(h.nsplit);
+    if (h.nsplit)
+      CU(cudaMemcpy(splits.data(), g.s_split.p, sizeof(int4) * h.nsplit, cudaMemcpyDeviceToHost));
+    headc.clear();
+    for (const int4& r : splits) split_item(r, dense_span, headc);
+    for (int4& r : headc) r.w &= ~kItemSingle;
+    nw = 0;
+    u64 nc2 = 0;
+    CU(build_queue(g, *cq2, headc, sp<int4>(*cq), nc, nc, &nc2));
+    std::swap(cq, cq2);
+    nc = nc2;
+    if (npartial + nc + 16 > partial_cap) {
+      // grow the partial store, keeping what is there
+      const u64 cap2 = (npartial + nc) * 2 + 16;
+      Graph::Scratch np, nh;
+      CU(cudaMalloc(&np.p, sizeof(TopEnt) * cap2 * k));
+      np.bytes = sizeof(TopEnt) * cap2 * k;
+      CU(cudaMalloc(&nh.p, sizeof(int2) * cap2));
+      nh.bytes = sizeof(int2) * cap2;
+      CU(cudaMemcpyAsync(np.p, g.s_partial.p, sizeof(TopEnt) * npartial * k,
+                         cudaMemcpyDeviceToDevice, st));
+      CU(cudaMemcpyAsync(nh.p, g.s_phdr.p, sizeof(int2) * npartial, cudaMemcpyDeviceToDevice, st));
+      CU(cudaStreamSynchronize(st));
+      cudaFree(g.s_partial.p);
+      cudaFree(g.s_phdr.p);
+      g.s_partial = np;
+      g.s_phdr = nh;
+      partial_cap = cap2;
+    }
+  }
+  tm.mark(2);
+  // merge the partial lists of split sources
+  if (npartial) {
+    std::vector<int2> hdr(npartial);
+    CU(cudaMemcpy(hdr.data(), g.s_phdr.p, sizeof(int2) * npartial, cudaMemcpyDeviceToHost));
+    std::vector<int> order(npartial);
+    for (u64 i = 0; i < npartial; ++i) order[i] = (int)i;
+    std::sort(order.begin(), order.end(),
+              [&](int x, int y) { return hdr[x].x != hdr[y].x ? hdr[x].x < hdr[y].x : x < y; });
+    std::vector<int4> grp;
+    for (u64 i = 0; i < npartial;) {
+      u64 j = i;
+      while (j < npartial && hdr[order[j]].x == hdr[order[i]].x) ++j;
+      grp.push_back(make_int4(hdr[order[i]].x, (int)i, (int)(j - i), 0));
+      i = j;
+    }
+    Graph::Scratch& tmp = g.s_failed;
+    const size_t need = sizeof(int4) * grp.size() + sizeof(int) * order.size() + 64;
+    CU(ensure(g, tmp, need));
+    int4* d_grp = sp<int4>(tmp);
+    int* d_order = reinterpret_cast<int*>(d_grp + grp.size());
+    CU(cudaMemcpyAsync(d_grp, grp.data(), sizeof(int4) * grp.size(), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, st));
+    CU(launch_merge_partials(d_grp, (int)grp.size(), d_order, sp<TopEnt>(g.s_partial),
+                             sp<int2>(g.s_phdr), k, sp<TopEnt>(g.s_top), d_counts, st));
+    t_stats.launches++;
+    CU(cudaStreamSynchronize(st));
+  }
+  CU(launch_emit_sources(sp<TopEnt>(g.s_top), d_counts, d_src, n_src, k, measure, g.fixbits, d_out,
+                         st));
+  t_stats.launches++;
+  if (measure == LP_AA || measure == LP_RA) {
+    CU(launch_pair_cn(d_out, d_counts, k, (u64)n_src * k, g.d_off, g.d_idx, g.d_deg, A.cap, st));
+    t_stats.launches++;
+  }
+  tm.mark(3);
+  CU(cudaStreamSynchronize(st));
+  t_stats.ms_estimate = tm.ms(0, 1);
+  t_stats.ms_scan = tm.ms(1, 2);
+  t_stats.ms_select = tm.ms(2, 3);
+  t_stats.ms_total = tm.ms(0, 3);
+  return LP_OK;
+}
+
+static lp_status check_sources_args(const lp_graph* g, int measure, const void* sources, int n_src,
+                                    int k, const void* out, const void* counts) {
+  if (!g) return fail(LP_EINVAL, "lp_predict_sources: null graph");
+  if (measure < 0 || measure > LP_RA) return fail(LP_EINVAL, "lp_predict_sources: bad measure");
+  if (n_src < 0) return fail(LP_EINVAL, "lp_predict_sources: n_src < 0");
+  if (k < 1 || k > LP_MAX_TOPK_PER_SOURCE)
+    return fail(LP_EINVAL, "lp_predict_sources: k must be in [1, %d]", LP_MAX_TOPK_PER_SOURCE);
+  if (n_src > 0 && (!sources || !out || !counts))
+    return fail(LP_EINVAL, "lp_predict_sources: null buffer");
+  return LP_OK;
+}
+
+}  // namespace lp
+
+extern "C" {
+
+lp_status lp_predict(const lp_graph* g, lp_measure measure, int32_t degree_cap, int64_t k,
+                     double threshold, lp_link* out, int64_t out_cap, int64_t* out_n) {
+  if (!g || !out_n) return lp::fail(LP_EINVAL, "lp_predict: null argument");
+  return lp::predict_global(*const_cast<lp_graph*>(g), (int)measure, degree_cap, k, threshold, out,
+                            false, out_cap, out_n);
+}
+
+lp_status lp_predict_dev(const lp_graph* g, lp_measure measure, int32_t degree_cap, int64_t k,
+                         double threshold, lp_link* d_out, int64_t out_cap, int64_t* out_n) {
+  if (!g || !out_n) return lp::fail(LP_EINVAL, "lp_predict_dev: null argument");
+  return lp::predict_global(*const_cast<lp_graph*>(g), (int)measure, degree_cap, k, threshold,
+                            d_out, true, out_cap, out_n);
+}
+
+lp_status lp_predict_sources_dev(const lp_graph* g, lp_measure measure, int32_t degree_cap,
+                                 const int32_t* d_sources, int32_t n_src, int32_t k,
+                                 double threshold, lp_link* d_out, int32_t* d_counts) {
+  lp::begin_stats();
+  lp_status s = lp::check_sources_args(g, (int)measure, d_sources, n_src, k, d_out, d_counts);
+  if (s != LP_OK) return s;
+  lp::Graph& gg = *const_cast<lp_graph*>(g);
+  std::lock_guard<std::mutex> lock(gg.mu);
+  cudaError_t e = cudaSetDevice(gg.device);
+  if (e != cudaSuccess) return lp::cuda_fail(e, "cudaSetDevice");
+  return lp::predict_sources(gg, (int)measure, degree_cap, d_sources, n_src, k, threshold, d_out,
+                             d_counts);
+}
+
+lp_status lp_predict_sources(const lp_graph* g, lp_measure measure, int32_t degree_cap,
+                             const int32_t* sources, int32_t n_src, int32_t k, double threshold,
+                             lp_link* out, int32_t* counts) {
+  lp::begin_stats();
+  lp_status s = lp::check_sources_args(g, (int)measure, sources, n_src, k, out, counts);
+  if (s != LP_OK) return s;
+  if (n_src == 0) return LP_OK;
+  for (int32_t i = 0; i < n_src; ++i)
+    if (sources[i] < 0 || sources[i] >= g->n)
+      return lp::fail(LP_EINVAL, "lp_predict_sources: source %d out of range", sources[i]);
+  lp::Graph& gg = *const_cast<lp_graph*>(g);
+  std::lock_guard<std::mutex> lock(gg.mu);
+  cudaError_t e = cudaSetDevice(gg.device);
+  if (e != cudaSuccess) return lp::cuda_fail(e, "cudaSetDevice");
+  const size_t nl = (size_t)n_src * k;
+  e = lp::ensure(gg, gg.s_src, sizeof(int) * n_src);
+  if (e == cudaSuccess) e = lp::ensure(gg, gg.s_links, sizeof(lp_link) * nl);
+  if (e == cudaSuccess) e = lp::ensure(gg, gg.s_cnt, sizeof(int) * n_src);
+  if (e != cudaSuccess) return lp::cuda_fail(e, "lp_predict_sources: scratch");
+  e = cudaMemcpyAsync(gg.s_src.p, sources, sizeof(int) * n_src, cudaMemcpyHostToDevice, gg.stream);
+  if (e != cudaSuccess) return lp::cuda_fail(e, "lp_predict_sources: upload");
+  s = lp::predict_sources(gg, (int)measure, degree_cap, lp::sp<int>(gg.s_src), n_src, k, threshold,
+                          lp::sp<lp_link>(gg.s_links), lp::sp<int>(gg.s_cnt));
+  if (s != LP_OK) return s;
+  e = cudaMemcpyAsync(out, gg.s_links.p, sizeof(lp_link) * nl, cudaMemcpyDeviceToHost, gg.stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(counts, gg.s_cnt.p, sizeof(int) * n_src, cudaMemcpyDeviceToHost, gg.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(gg.stream);
+  if (e != cudaSuccess) return lp::cuda_fail(e, "lp_predict_sources: download");
+  return LP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,195 @@
+// lp_internal.cuh -- shared declarations of the liblp CUDA implementation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "lp.h"
+
+namespace lp {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+constexpr int kEmpty = -1;               // empty hash key
+constexpr int kWarpSlots = 1024;         // per-warp hash table (warp tier)
+constexpr int kWarpMaxWedges = 512;      // warp tier: W(a) <= this
+constexpr int kCtaThreads = 512;         // CTA items
+constexpr int kCtaWarps = kCtaThreads / 32;
+constexpr int kCtaSlots = 16384;         // CTA hash table slots
+constexpr int kCtaMaxWedges = 8192;      // single-item hash: W <= this
+constexpr int kSplitTarget = 6144;       // wedges per split hash item
+constexpr int kCtaSmem = 192 * 1024;     // dynamic shared memory of a CTA item
+constexpr int kWarpTierThreads = 256;
+
+// Item kinds (int4.w of a CTA work record).
+constexpr int kItemDense = 1;    // dense counters over [lo, hi)
+constexpr int kItemSingle = 2;   // the only item of its source (per-source mode)
+
+// Arc table entry for arc e = (a -> b): x = position of a in Gamma_b
+// (absolute index into idx), y = off[b + 1], z = |Gamma_b|, w = b.
+typedef int4 Arc;
+
+// Selection candidate: exact key num/den, pair (u, v).
+struct __align__(8) Cand {
+  u64 num, den;
+  int u, v;
+};
+
+// Per-source top-k entry.
+struct __align__(8) TopEnt {
+  u64 num, den;
+  int c, cn;
+};
+
+// Admission threshold: candidates must rank strictly before it.
+struct Thresh {
+  u64 num, den;
+  int u, v;
+  int valid;
+  int pad;
+};
+
+// Device-side counters of one predict call (one allocation, read back whole).
+struct Counters {
+  u64 wedges;        // estimate: wedges of scanned sources
+  u64 kept_arcs;
+  u64 scanned_arcs;
+  u64 nwarp;         // warp queue length written by the estimate kernel
+  u64 nitem;         // CTA item queue length written by the estimate kernel
+  u64 claim_w;       // dynamic claim counters
+  u64 claim_c;
+  u64 cand_cnt;      // selection buffer fill (may exceed capacity)
+  u64 candidates;    // distinct candidates scored
+  u64 nfailed;       // failed records (buffer overflow)
+  u64 nsplit;        // overflowed hash items
+  u64 npartial;      // per-source partial lists written
+  u64 dense_items;
+  u64 tier_wedges[2];
+  u64 tier_arcs[2];
+  u64 tier_kept[2];
+  u32 full;          // selection buffer full
+  u32 error;         // device consistency error code
+  u64 pad[2];
+};
+
+// Everything a scan kernel needs (passed by value).
+struct ScanArgs {
+  const int* off;
+  const int* idx;
+  const int* deg;
+  const Arc* arc;
+  int n;
+  int cap;            // hub limit; INT32_MAX for none
+  int measure;
+  int mode;           // 0 global (c > a), 1 per-source (c != a)
+  int fixbits;        // AA/RA fixed-point fraction bits
+  int thr_check;      // 1 if the S_th test is needed (threshold > 0)
+  double threshold;
+  const int* sources; // per-source mode: source vertex of record index
+  Counters* ctr;
+  // global mode selection buffer
+  Cand* buf;
+  u64 buf_cap;
+  const Thresh* thresh;
+  // failure / split records
+  int4* failed;
+  u64 failed_cap;
+  int4* split;
+  u64 split_cap;
+  // per-source mode outputs
+  int k;
+  TopEnt* out_top;     // [n_src * k] final lists (single items / warp tier)
+  int* out_cnt;        // [n_src]
+  TopEnt* partial;     // [partial_cap * k] lists of split items
+  int2* partial_hdr;   // [partial_cap] (record index, count)
+  u64 partial_cap;
+  // binning parameters
+  int warp_max;        // warp tier: W <= warp_max (<= kWarpMaxWedges)
+  int cta_max;         // single CTA item: W <= cta_max (<= kCtaMaxWedges)
+  int split_target;    // wedges per split hash item
+  int split_logcap;    // log2 slots of split hash items (<= log2 kCtaSlots)
+};
+
+// Process-wide tuning options (lp_set_option).
+struct Options {
+  long long select_buffer = 8ll << 20;
+  int warp_max = kWarpMaxWedges;
+  int cta_max = kCtaMaxWedges;
+  int split_target = kSplitTarget;
+  int split_logcap = 14;
+};
+Options options_snapshot();
+
+// Host-side graph object.
+struct Graph {
+  int device = 0;
+  int32_t n = 0;
+  int64_t arcs = 0;
+  int32_t dmax = 0;
+  int fixbits = 40;
+  cudaStream_t stream = nullptr;
+  int* d_off = nullptr;
+  int* d_idx = nullptr;
+  int* d_deg = nullptr;
+  Arc* d_arc = nullptr;
+  std::mutex mu;
+  // scratch, grown on demand
+  struct Scratch {
+    void* p = nullptr;
+    size_t bytes = 0;
+  };
+  Scratch s_ctr, s_w, s_warpq, s_itemq, s_warpq2, s_itemq2, s_buf, s_buf2, s_failed, s_split,
+      s_thresh, s_flags, s_partial, s_phdr, s_top, s_cnt, s_links, s_src, s_grp;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};  // per-kernel timing
+};
+
+// ---------------------------------------------------------------- device --
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// Exact total order: x strictly before y (score desc, u asc, v asc).
+__device__ __forceinline__ bool before(u64 xn, u64 xd, int xu, int xv, u64 yn, u64 yd, int yu,
+                                       int yv) {
+  u64 lh = __umul64hi(xn, yd), ll = xn * yd;
+  u64 rh = __umul64hi(yn, xd), rl = yn * xd;
+  if (lh != rh) return lh > rh;
+  if (ll != rl) return ll > rl;
+  if (xu != yu) return xu < yu;
+  return xv < yv;
+}
+
+__device__ __forceinline__ bool cand_before(const Cand& x, const Cand& y) {
+  return before(x.num, x.den, x.u, x.v, y.num, y.den, y.u, y.v);
+}
+
+}  // namespace lp
+
+// Host-side launchers implemented in the .cu files.
+namespace lp {
+inline u64 sort_splits_needed(u64 n) { return n / 2048 + 2; }
+cudaError_t launch_sort_cands(Cand* d_a, Cand* d_tmp, int* splits, u64 n, cudaStream_t st,
+                              Cand** result, int* launches);
+cudaError_t launch_set_thresh(const Cand* sorted, u64 k, Thresh* t, cudaStream_t st);
+cudaError_t launch_estimate(const ScanArgs& A, int n_rec, int4* warpq, int4* itemq, u64 itemq_cap,
+                            int2* grp, cudaStream_t st);
+cudaError_t launch_scan_warp(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
+cudaError_t launch_scan_cta(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
+cudaError_t launch_merge_partials(const int4* grp_list, int ngrp, const int* order,
+                                  const TopEnt* partial, const int2* hdr, int k, TopEnt* out_top,
+                                  int* out_cnt, cudaStream_t st);
+cudaError_t launch_emit_global(const Cand* c, u64 n, int measure, int fixbits, lp_link* out,
+                               cudaStream_t st);
+cudaError_t launch_emit_sources(const TopEnt* top, const int* cnt, const int* sources, int n_src,
+                                int k, int measure, int fixbits, lp_link* out, cudaStream_t st);
+cudaError_t launch_pair_cn(lp_link* links, const int* cnt_rows, int k, u64 n, const int* off,
+                           const int* idx, const int* deg, int cap, cudaStream_t st);
+cudaError_t launch_filter_failed(Cand* d_buf, u64 n, const unsigned char* d_flag,
+                                 const int4* d_failed_sorted, int nfailed, Cand* d_out,
+                                 Counters* d_ctr, u64* d_count, cudaStream_t st);
+}  // namespace lp
