@@ -134,15 +134,23 @@ def traffic_record(kernel: str):
     return ent.get("dram_bytes_per_launch")
 
 
+_ARGS = None
+
+
 def make_workload():
     import lp_inputs as L
-    g = L.cfg_rmat20(seed=1)
+    scale = _ARGS.scale if _ARGS is not None else 20
+    g = L.rmat(scale, 16, seed=1)
     split = L.holdout(g, 0.1, seed=43)
     return split
 
 
 def step_calls():
-    return [(m, c) for c in CAPS for m in MEASURES]
+    calls = [(m, c) for c in CAPS for m in MEASURES]
+    if _ARGS is not None and _ARGS.only:
+        want = set(_ARGS.only.split(","))
+        calls = [(m, c) for m, c in calls if f"{m}@{'inf' if c is None else c}" in want]
+    return calls
 
 
 # ------------------------------------------------------------- our arm ----
@@ -154,6 +162,8 @@ def run_ours(args, rank, world, local_rank):
     from paper_2401_11415_gb300 import _build
     _build.build()
 
+    if args.select_buffer:
+        lp.lp_set_option(lp.LP_OPT_SELECT_BUFFER, args.select_buffer)
     split = make_workload()
     obs = split.observed
     k = len(split.hu)
@@ -192,13 +202,13 @@ def run_ours(args, rank, world, local_rank):
     dist_barrier(world)
 
     # e2e through the host-buffer API (graph upload + host outputs)
-    e2e = run_e2e(lp, torch, obs, k, max(1, min(args.steps, 3)))
+    e2e = None if args.no_e2e else run_e2e(lp, torch, obs, k, max(1, min(args.steps, 3)))
 
     # roofline of the dominant scan kernel
-    tier_ms = [sum(s["tier_ms"][i] for s in stats) for i in range(2)]
-    tier_launch = [sum(s["tier_launches"][i] for s in stats) for i in range(2)]
-    dom = 0 if tier_ms[0] >= tier_ms[1] else 1
-    name = ["k_scan_warp", "k_scan_cta"][dom]
+    tier_ms = [sum(s["tier_ms"][i] for s in stats) for i in range(3)]
+    tier_launch = [sum(s["tier_launches"][i] for s in stats) for i in range(3)]
+    dom = max(range(3), key=lambda i: tier_ms[i])
+    name = ["k_scan_warp", "k_scan_cta", "k_scan_big"][dom]
     alg_bytes = 0
     for s in stats:
         alg_bytes += (4 * s["tier_arcs"][dom] + 4 * s["tier_arcs"][dom] + 4 * s["tier_kept"][dom]
@@ -244,6 +254,8 @@ def run_ours(args, rank, world, local_rank):
         "per_call_ms": {k_: round(v / args.steps, 3) for k_, v in per_cap.items()},
         "clocks": clk.summary(),
     }
+    if args.scale != 20 or args.only:
+        line["config"]["workload"] += f" [subset: scale {args.scale}, calls {args.only or 'all'}]"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(split)
     G.close()
@@ -374,7 +386,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", default="", help="subset of calls, e.g. JC@inf,RA@256")
+    ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (20 = the workload)")
+    ap.add_argument("--select-buffer", type=int, default=0,
+                    help="minimum selection-buffer capacity (candidates); 0 = library default")
     args = ap.parse_args()
+    global _ARGS
+    _ARGS = args
     rank, world, local = dist_init()
     if args.impl == "reference":
         line = run_reference(args, rank, world)

@@ -103,12 +103,15 @@ typedef struct {
   float ms_scan;
   float ms_select;
   float ms_total;
-  /* per scan kernel: [0] warp tier, [1] CTA items */
-  int64_t tier_wedges[2];  /* wedges of the sources binned to the tier       */
-  int64_t tier_arcs[2];    /* arc-table entries read by the tier             */
-  int64_t tier_kept[2];    /* of which pass the hub test                     */
-  int32_t tier_launches[2];/* launches of the tier's scan kernel             */
-  float tier_ms[2];        /* summed device time of those launches (timing on) */
+  /* per scan kernel: [0] warp tier, [1] medium tier, [2] large tier */
+  int64_t tier_wedges[3];  /* wedges of the sources binned to the tier       */
+  int64_t tier_arcs[3];    /* arc-table entries read by the tier             */
+  int64_t tier_kept[3];    /* of which pass the hub test                     */
+  int32_t tier_launches[3];/* launches of the tier's scan kernel             */
+  float tier_ms[3];        /* summed device time of those launches (timing on) */
+  int64_t phase_cycles[6]; /* LP_OPT_PHASE_PROFILE: SM cycles of the large tier
+                              (summed over CTAs) in item setup, own arcs, shared
+                              pieces, exclusion, scoring, item end            */
 } lp_stats;
 
 /*
@@ -175,10 +178,16 @@ lp_status lp_predict_sources_dev(const lp_graph* g, lp_measure measure, int32_t 
 typedef enum {
   LP_OPT_SELECT_BUFFER = 1,   /* minimum selection-buffer capacity in candidates
                                  (default 8388608; 24 bytes each, twice)       */
-  LP_OPT_WARP_MAX_WEDGES = 2, /* warp tier: sources with W <= this (1..512, 512) */
-  LP_OPT_CTA_MAX_WEDGES = 3,  /* one CTA item per source up to W (513..8192, 8192) */
+  LP_OPT_WARP_MAX_WEDGES = 2, /* warp tier: sources with W <= this (1..256, 256) */
+  LP_OPT_CTA_MAX_WEDGES = 3,  /* one large item per source up to W (257..8192, 8192) */
   LP_OPT_SPLIT_TARGET = 4,    /* wedges per split hash item (256..12288, 6144) */
-  LP_OPT_SPLIT_LOGCAP = 5     /* log2 slots of a split hash item (6..14, 14)     */
+  LP_OPT_SPLIT_LOGCAP = 5,    /* log2 slots of a split hash item (6..14, 14)     */
+  LP_OPT_MED_MAX_WEDGES = 6,  /* medium tier: W <= this (1..1024, 1024); the
+                                 warp tier takes precedence                     */
+  LP_OPT_ITEM_WEDGES = 7,     /* target wedges of one dense sweep item
+                                 (1024..2^30, 262144)                           */
+  LP_OPT_PHASE_PROFILE = 8    /* 1: record per-phase clock cycles of the large
+                                 tier in lp_stats.phase_cycles (0..1, 0)        */
 } lp_option;
 
 /* Set a tuning option; LP_EINVAL if the option or value is out of range. */

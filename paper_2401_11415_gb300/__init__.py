@@ -43,9 +43,10 @@ class lp_stats(ctypes.Structure):
                 ("splits", ctypes.c_int32), ("compactions", ctypes.c_int32),
                 ("launches", ctypes.c_int32), ("ms_estimate", ctypes.c_float),
                 ("ms_scan", ctypes.c_float), ("ms_select", ctypes.c_float),
-                ("ms_total", ctypes.c_float), ("tier_wedges", ctypes.c_int64 * 2),
-                ("tier_arcs", ctypes.c_int64 * 2), ("tier_kept", ctypes.c_int64 * 2),
-                ("tier_launches", ctypes.c_int32 * 2), ("tier_ms", ctypes.c_float * 2)]
+                ("ms_total", ctypes.c_float), ("tier_wedges", ctypes.c_int64 * 3),
+                ("tier_arcs", ctypes.c_int64 * 3), ("tier_kept", ctypes.c_int64 * 3),
+                ("tier_launches", ctypes.c_int32 * 3), ("tier_ms", ctypes.c_float * 3),
+                ("phase_cycles", ctypes.c_int64 * 6)]
 
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -217,7 +218,8 @@ def lp_predict_sources_dev(h, measure, d_sources, n_src: int, k: int, degree_cap
 
 
 LP_OPT_SELECT_BUFFER, LP_OPT_WARP_MAX_WEDGES, LP_OPT_CTA_MAX_WEDGES, LP_OPT_SPLIT_TARGET, \
-    LP_OPT_SPLIT_LOGCAP = range(1, 6)
+    LP_OPT_SPLIT_LOGCAP, LP_OPT_MED_MAX_WEDGES, LP_OPT_ITEM_WEDGES, LP_OPT_PHASE_PROFILE = \
+    range(1, 9)
 
 
 def lp_set_option(option: int, value: int) -> None:

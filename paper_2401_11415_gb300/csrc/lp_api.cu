@@ -127,7 +127,8 @@ static void free_graph(Graph* g) {
   if (!g) return;
   if (g->stream) cudaStreamSynchronize(g->stream);
   Graph::Scratch* all[] = {&g->s_ctr, &g->s_w, &g->s_warpq, &g->s_itemq, &g->s_warpq2,
-                           &g->s_itemq2, &g->s_buf, &g->s_buf2, &g->s_failed, &g->s_split,
+                           &g->s_itemq2, &g->s_medq, &g->s_medq2, &g->s_buf, &g->s_buf2,
+                           &g->s_buf3, &g->s_misc, &g->s_failed, &g->s_split,
                            &g->s_thresh, &g->s_flags, &g->s_partial, &g->s_phdr, &g->s_top,
                            &g->s_cnt, &g->s_links, &g->s_src, &g->s_grp};
   for (auto* s : all)
@@ -165,8 +166,20 @@ lp_status lp_set_option(lp_option option, int64_t value) {
       if (value < 1 || value > lp::kWarpMaxWedges) break;
       lp::g_opt.warp_max = (int)value;
       return LP_OK;
+    case LP_OPT_MED_MAX_WEDGES:
+      if (value < 1 || value > lp::kMedMaxWedges) break;
+      lp::g_opt.med_max = (int)value;
+      return LP_OK;
+    case LP_OPT_ITEM_WEDGES:
+      if (value < 1024 || value > (1ll << 30)) break;
+      lp::g_opt.item_wedges = value;
+      return LP_OK;
+    case LP_OPT_PHASE_PROFILE:
+      if (value < 0 || value > 1) break;
+      lp::g_opt.phase_profile = (int)value;
+      return LP_OK;
     case LP_OPT_CTA_MAX_WEDGES:
-      if (value < 513 || value > lp::kCtaMaxWedges) break;
+      if (value < 257 || value > lp::kCtaMaxWedges) break;
       lp::g_opt.cta_max = (int)value;
       return LP_OK;
     case LP_OPT_SPLIT_TARGET:
@@ -192,6 +205,9 @@ int64_t lp_get_option(lp_option option) {
     case LP_OPT_CTA_MAX_WEDGES: return o.cta_max;
     case LP_OPT_SPLIT_TARGET: return o.split_target;
     case LP_OPT_SPLIT_LOGCAP: return o.split_logcap;
+    case LP_OPT_MED_MAX_WEDGES: return o.med_max;
+    case LP_OPT_ITEM_WEDGES: return o.item_wedges;
+    case LP_OPT_PHASE_PROFILE: return o.phase_profile;
     default: return -1;
   }
 }
@@ -295,7 +311,7 @@ lp_status lp_graph_create(int32_t n, const int32_t* offsets, const int32_t* indi
   if (e == cudaSuccess) e = cudaMalloc(&g->d_arc, sizeof(Arc) * (size_t)(A > 0 ? A : 1));
   if (e == cudaSuccess) e = cudaMalloc(&d_err, sizeof(int));
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->ev[i]);
-  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->kev[i]);
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->kev[i]);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(g->d_off, offsets, sizeof(int) * ((size_t)n + 1), cudaMemcpyHostToDevice,
                         g->stream);
@@ -353,29 +369,40 @@ struct Timer {
   }
 };
 
-// Launch both scan kernels; with timing on, time each on the graph's stream.
-static cudaError_t scan_launches(Graph& g, const ScanArgs& A, const int4* wq, u64 nw,
-                                 const int4* cq, u64 nc, bool timing) {
+// The three work queues (warp tier, medium tier, large tier).  cur[t] holds
+// the records of the next launch, alt[t] receives the rebuilt queue.
+struct Queues {
+  Graph::Scratch* cur[3];
+  Graph::Scratch* alt[3];
+  u64 n[3];
+};
+
+// Launch the scan kernels; with timing on, time each on the graph's stream.
+static cudaError_t scan_launches(Graph& g, const ScanArgs& A, const Queues& Q, bool timing) {
   cudaStream_t st = g.stream;
-  if (timing && nw) cudaEventRecord(g.kev[0], st);
-  cudaError_t e = launch_scan_warp(A, wq, nw, st);
-  if (e != cudaSuccess) return e;
-  if (timing && nw) cudaEventRecord(g.kev[1], st);
-  if (timing && nc) cudaEventRecord(g.kev[2], st);
-  e = launch_scan_cta(A, cq, nc, st);
-  if (e != cudaSuccess) return e;
-  if (timing && nc) cudaEventRecord(g.kev[3], st);
-  if (nw) t_stats.tier_launches[0]++;
-  if (nc) t_stats.tier_launches[1]++;
+  for (int t = 2; t >= 0; --t) {  // largest work first
+    if (!Q.n[t]) continue;
+    if (timing) cudaEventRecord(g.kev[2 * t], st);
+    const int4* q = sp<int4>(*Q.cur[t]);
+    cudaError_t e = t == 0 ? launch_scan_warp(A, q, Q.n[t], st)
+                           : (t == 1 ? launch_scan_med(A, q, Q.n[t], st)
+                                     : launch_scan_cta(A, q, Q.n[t], st));
+    if (e != cudaSuccess) return e;
+    if (timing) cudaEventRecord(g.kev[2 * t + 1], st);
+    t_stats.tier_launches[t]++;
+    t_stats.launches++;
+  }
   return cudaSuccess;
 }
 
 // After the stream synchronised: add the kernels' event times to the stats.
-static void scan_times(Graph& g, u64 nw, u64 nc, bool timing) {
+static void scan_times(Graph& g, const Queues& Q, bool timing) {
   if (!timing) return;
-  float t = 0.f;
-  if (nw && cudaEventElapsedTime(&t, g.kev[0], g.kev[1]) == cudaSuccess) t_stats.tier_ms[0] += t;
-  if (nc && cudaEventElapsedTime(&t, g.kev[2], g.kev[3]) == cudaSuccess) t_stats.tier_ms[1] += t;
+  for (int t = 0; t < 3; ++t) {
+    float ms = 0.f;
+    if (Q.n[t] && cudaEventElapsedTime(&ms, g.kev[2 * t], g.kev[2 * t + 1]) == cudaSuccess)
+      t_stats.tier_ms[t] += ms;
+  }
 }
 
 static void estimate_stats(const Counters& h) {
@@ -383,23 +410,38 @@ static void estimate_stats(const Counters& h) {
   t_stats.kept_arcs = (int64_t)h.kept_arcs;
   t_stats.scanned_arcs = (int64_t)h.scanned_arcs;
   t_stats.warp_sources = (int32_t)h.nwarp;
-  t_stats.cta_items = (int32_t)h.nitem;
+  t_stats.cta_items = (int32_t)(h.nmed + h.nitem);
   t_stats.dense_items = (int32_t)h.dense_items;
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 3; ++i) {
     t_stats.tier_wedges[i] = (int64_t)h.tier_wedges[i];
     t_stats.tier_arcs[i] = (int64_t)h.tier_arcs[i];
     t_stats.tier_kept[i] = (int64_t)h.tier_kept[i];
   }
 }
 
-static ScanArgs base_args(Graph& g, int measure, int cap, double threshold, int mode) {
+static ScanArgs base_args(Graph& g, int measure, int cap, double threshold, int mode, int k) {
   ScanArgs A;
   memset(&A, 0, sizeof(A));
   const Options o = options_snapshot();
-  A.warp_max = o.warp_max;
-  A.cta_max = o.cta_max;
+  const bool v64 = measure == LP_AA || measure == LP_RA;
+  const int vbytes = v64 ? 8 : 4;
+  int big_bytes = kCtaSmem;
+  if (mode == 1) {
+    const int avail = 227 * 1024 - 2048 - kBigExtraSmem - kCtaWarps * k * (int)sizeof(TopEnt);
+    if (avail < big_bytes) big_bytes = avail & ~1023;
+  }
+  int big_logcap = 0;
+  while ((2ll << big_logcap) * (4 + vbytes) <= big_bytes) ++big_logcap;
+  A.big_bytes = big_bytes;
+  A.big_logcap = big_logcap;
+  // dense window: counters plus one touched bit per counter, 128-aligned
+  A.big_span = (int)(((long long)big_bytes * 8 / (8 * vbytes + 1)) & ~127ll);
+  A.warp_max = std::min(o.warp_max, kWarpMaxWedges);
+  A.med_max = std::max(A.warp_max, std::min(o.med_max, kMedMaxWedges));
+  A.cta_max = std::max(A.med_max, std::min(o.cta_max, 1 << (big_logcap - 1)));
   A.split_target = o.split_target;
-  A.split_logcap = o.split_logcap;
+  A.item_wedges = (int)o.item_wedges;
+  A.split_logcap = std::min(o.split_logcap, big_logcap);
   A.off = g.d_off;
   A.idx = g.d_idx;
   A.deg = g.d_deg;
@@ -411,6 +453,8 @@ static ScanArgs base_args(Graph& g, int measure, int cap, double threshold, int 
   A.fixbits = g.fixbits;
   A.thr_check = (threshold <= 0.0) ? 0 : 1;  // scores are > 0; NaN keeps the test
   A.threshold = threshold;
+  A.k = k;
+  A.prof = nullptr;
   return A;
 }
 
@@ -418,11 +462,13 @@ static ScanArgs base_args(Graph& g, int measure, int cap, double threshold, int 
 static void split_item(const int4& r, int dense_span, std::vector<int4>& out) {
   const int lo = r.y, hi = r.z;
   const int logcap = (r.w >> 8) & 0xff;
+  const int keep = r.w & kItemSingle;
   if (hi - lo <= dense_span) {
     out.push_back(make_int4(r.x, lo, hi, kItemDense | (logcap << 8)));
     return;
   }
   const int mid = lo + (hi - lo) / 2;
+  (void)keep;
   out.push_back(make_int4(r.x, lo, mid, (logcap << 8)));
   out.push_back(make_int4(r.x, mid, hi, (logcap << 8)));
 }
@@ -441,8 +487,28 @@ static cudaError_t build_queue(Graph& g, Graph::Scratch& dst, const std::vector<
   if (e == cudaSuccess && rem)
     e = cudaMemcpyAsync(sp<int4>(dst) + head.size(), src + from, sizeof(int4) * rem,
                         cudaMemcpyDeviceToDevice, g.stream);
-  if (e == cudaSuccess && !head.empty()) e = cudaStreamSynchronize(g.stream);  // head is stack data
+  if (e == cudaSuccess && !head.empty()) e = cudaStreamSynchronize(g.stream);
   return e;
+}
+
+// Rebuild the three queues: re-queued records first, then the unclaimed
+// remainder of each queue.
+static cudaError_t rebuild_queues(Graph& g, Queues& Q, const std::vector<int4>* heads,
+                                  const u64* done) {
+  for (int t = 0; t < 3; ++t) {
+    u64 n2 = 0;
+    cudaError_t e = build_queue(g, *Q.alt[t], heads[t], sp<int4>(*Q.cur[t]), done[t], Q.n[t], &n2);
+    if (e != cudaSuccess) return e;
+    std::swap(Q.cur[t], Q.alt[t]);
+    Q.n[t] = n2;
+  }
+  return cudaSuccess;
+}
+
+static int record_tier(const int4& r) {
+  if (r.w & (1 << 30)) return 0;
+  if (r.w & (1 << 29)) return 1;
+  return 2;
 }
 
 __global__ void k_set_flags(const int4* __restrict__ rec, int n, unsigned char* __restrict__ flag,
@@ -456,7 +522,61 @@ __global__ void k_check_sources(const int* __restrict__ s, int n_src, int n, int
   if (i < n_src && (s[i] < 0 || s[i] >= n)) atomicExch(bad, 1);
 }
 
+// Estimate and bin; re-run once with a larger item queue if it overflowed.
+static lp_status run_estimate(Graph& g, ScanArgs& A, int n_rec, int2* grp, Counters& h) {
+  cudaStream_t st = g.stream;
+  Counters* d_ctr = sp<Counters>(g.s_ctr);
+  CU(ensure(g, g.s_warpq, sizeof(int4) * ((size_t)n_rec + 1)));
+  CU(ensure(g, g.s_medq, sizeof(int4) * ((size_t)n_rec + 1)));
+  u64 itemq_cap = std::max<u64>(1024, g.s_itemq.bytes / sizeof(int4));
+  CU(ensure(g, g.s_itemq, sizeof(int4) * itemq_cap));
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    CU(cudaMemsetAsync(d_ctr, 0, sizeof(Counters), st));
+    A.ctr = d_ctr;
+    CU(launch_estimate2(A, n_rec, sp<int4>(g.s_warpq), sp<int4>(g.s_medq), sp<int4>(g.s_itemq),
+                        itemq_cap, grp, st));
+    t_stats.launches++;
+    CU(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (h.nitem <= itemq_cap) break;
+    itemq_cap = h.nitem + 1024;
+    CU(ensure(g, g.s_itemq, sizeof(int4) * itemq_cap));
+  }
+  if (h.nitem > itemq_cap) return fail(LP_EINTERNAL, "item queue sizing");
+  estimate_stats(h);
+  return LP_OK;
+}
+
 // ---------------------------------------------------------- global mode --
+
+constexpr size_t kMiscBytes = sizeof(u32) * 2048 + 2 * sizeof(u64) + 512 * sizeof(Cand);
+
+static u32* misc_hist(Graph& g) { return sp<u32>(g.s_misc); }
+static u64* misc_cnt(Graph& g) { return reinterpret_cast<u64*>(sp<u32>(g.s_misc) + 2048); }
+static Cand* misc_worst(Graph& g) { return reinterpret_cast<Cand*>(misc_cnt(g) + 2); }
+
+// The best k of s_buf[0, m) by radix selection; on return s_buf holds them
+// (sorted = true: in order, first k of *n_out entries valid).  SC and LHN
+// keep their tie group on the FP64 key and are always sorted here.
+static cudaError_t select_best(Graph& g, int measure, u64 m, u64 k, u64* n_out, bool sorted) {
+  cudaStream_t st = g.stream;
+  u64 ns = 0;
+  cudaError_t e = radix_select(sp<Cand>(g.s_buf), m, k, measure, sp<Cand>(g.s_buf2),
+                               sp<Cand>(g.s_buf3), sp<Cand>(g.s_buf), misc_hist(g), misc_cnt(g), st,
+                               &ns, &t_stats.launches);
+  if (e != cudaSuccess) return e;
+  std::swap(g.s_buf, g.s_buf2);  // s_buf = the selected entries
+  const bool inexact = measure == LP_SC || measure == LP_LHN;
+  if (sorted || inexact) {
+    Cand* res = nullptr;
+    e = launch_sort_cands(sp<Cand>(g.s_buf), sp<Cand>(g.s_buf2), sp<int>(g.s_grp), ns, st, &res,
+                          &t_stats.launches);
+    if (e != cudaSuccess) return e;
+    if (res != sp<Cand>(g.s_buf)) std::swap(g.s_buf, g.s_buf2);
+  }
+  *n_out = ns;
+  return cudaSuccess;
+}
 
 static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, double threshold,
                                 lp_link* out, bool out_dev, int64_t out_cap, int64_t* out_n) {
@@ -471,56 +591,37 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
   cudaStream_t st = g.stream;
   Timer tm(g);
   tm.mark(0);
-  ScanArgs A = base_args(g, measure, cap, threshold, 0);
-  const int dense_span = (measure == LP_AA || measure == LP_RA) ? kCtaSmem / 8 : kCtaSmem / 4;
+  ScanArgs A = base_args(g, measure, cap, threshold, 0, 0);
   // selection buffer
   const u64 minbuf = (u64)std::max<long long>(16, options_snapshot().select_buffer);
   u64 C = k > 0 ? std::max<u64>(minbuf, 2ull * (u64)k + std::min<u64>(minbuf, 1ull << 20)) : minbuf;
   const u64 failed_cap = 1 << 20, split_cap = 1 << 20;
   CU(ensure(g, g.s_ctr, sizeof(Counters)));
   CU(ensure(g, g.s_thresh, sizeof(Thresh)));
-  CU(ensure(g, g.s_warpq, sizeof(int4) * ((size_t)g.n + 1)));
   CU(ensure(g, g.s_buf, sizeof(Cand) * C));
   CU(ensure(g, g.s_buf2, sizeof(Cand) * C));
+  CU(ensure(g, g.s_buf3, sizeof(Cand) * C));
+  CU(ensure(g, g.s_misc, kMiscBytes));
   CU(ensure(g, g.s_failed, sizeof(int4) * failed_cap));
   CU(ensure(g, g.s_split, sizeof(int4) * split_cap));
   CU(ensure(g, g.s_flags, (size_t)g.n + 1));
   CU(ensure(g, g.s_grp, sizeof(int) * sort_splits_needed(C)));
-  u64 itemq_cap = std::max<u64>(1024, g.s_itemq.bytes / sizeof(int4));
-  CU(ensure(g, g.s_itemq, sizeof(int4) * itemq_cap));
   Counters* d_ctr = sp<Counters>(g.s_ctr);
   Thresh* d_th = sp<Thresh>(g.s_thresh);
   CU(cudaMemsetAsync(d_th, 0, sizeof(Thresh), st));
   CU(cudaMemsetAsync(g.s_flags.p, 0, (size_t)g.n + 1, st));
   Counters h{};
-  // estimate + binning (re-run if the item queue was too small)
-  for (int attempt = 0; attempt < 3; ++attempt) {
-    CU(cudaMemsetAsync(d_ctr, 0, sizeof(Counters), st));
-    A.ctr = d_ctr;
-    CU(launch_estimate(A, g.n, sp<int4>(g.s_warpq), sp<int4>(g.s_itemq), itemq_cap, nullptr, st));
-    t_stats.launches++;
-    CU(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    if (h.nitem <= itemq_cap) break;
-    itemq_cap = h.nitem + 1024;
-    CU(ensure(g, g.s_itemq, sizeof(int4) * itemq_cap));
-  }
-  if (h.nitem > itemq_cap) return fail(LP_EINTERNAL, "lp_predict: item queue sizing");
-  estimate_stats(h);
+  lp_status s = run_estimate(g, A, g.n, nullptr, h);
+  if (s != LP_OK) return s;
   tm.mark(1);
 
-  // queues: current lists live in s_warpq / s_itemq; rebuilt lists go to the
-  // *2 buffers and are swapped in
-  Graph::Scratch* wq = &g.s_warpq;
-  Graph::Scratch* wq2 = &g.s_warpq2;
-  Graph::Scratch* cq = &g.s_itemq;
-  Graph::Scratch* cq2 = &g.s_itemq2;
-  u64 nw = h.nwarp, nc = h.nitem;
+  Queues Q = {{&g.s_warpq, &g.s_medq, &g.s_itemq}, {&g.s_warpq2, &g.s_medq2, &g.s_itemq2},
+              {h.nwarp, h.nmed, h.nitem}};
   u64 kept = 0;  // valid entries at the start of the buffer
-  std::vector<int4> failed, splits, headw, headc;
-  for (int round = 0; nw + nc > 0; ++round) {
+  std::vector<int4> failed, splits;
+  std::vector<int4> heads[3];
+  for (int round = 0; Q.n[0] + Q.n[1] + Q.n[2] > 0; ++round) {
     if (round > 100000) return fail(LP_EINTERNAL, "lp_predict: no progress");
-    // reset the per-launch counters, keep the buffer fill
     Counters z{};
     z.cand_cnt = kept;
     CU(cudaMemcpyAsync(d_ctr, &z, sizeof(Counters), cudaMemcpyHostToDevice, st));
@@ -532,11 +633,12 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
     A.failed_cap = failed_cap;
     A.split = sp<int4>(g.s_split);
     A.split_cap = split_cap;
-    CU(scan_launches(g, A, sp<int4>(*wq), nw, sp<int4>(*cq), nc, tm.on));
-    t_stats.launches += (nw > 0) + (nc > 0);
+    A.prof = options_snapshot().phase_profile ? d_ctr->prof : nullptr;
+    CU(scan_launches(g, A, Q, tm.on));
     CU(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    scan_times(g, nw, nc, tm.on);
+    scan_times(g, Q, tm.on);
+    for (int i = 0; i < 6; ++i) t_stats.phase_cycles[i] += (int64_t)h.prof[i];
     if (h.error) return fail(LP_EINTERNAL, "lp_predict: device check %u", h.error);
     t_stats.candidates += (int64_t)h.candidates;
     failed.resize(h.nfailed);
@@ -545,8 +647,9 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
       CU(cudaMemcpy(failed.data(), g.s_failed.p, sizeof(int4) * h.nfailed, cudaMemcpyDeviceToHost));
     if (h.nsplit)
       CU(cudaMemcpy(splits.data(), g.s_split.p, sizeof(int4) * h.nsplit, cudaMemcpyDeviceToHost));
-    const u64 done_w = std::min<u64>(h.claim_w, nw), done_c = std::min<u64>(h.claim_c, nc);
-    u64 valid = std::min<u64>(h.cand_cnt, C);
+    const u64 done[3] = {std::min<u64>(h.claim_w, Q.n[0]), std::min<u64>(h.claim_m, Q.n[1]),
+                         std::min<u64>(h.claim_c, Q.n[2])};
+    const u64 valid = std::min<u64>(h.cand_cnt, C);
     t_stats.splits += (int32_t)h.nsplit;
     if (h.full) {
       // compaction: drop failed output, then sort and cut to k
@@ -575,22 +678,19 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
         std::swap(g.s_buf, g.s_buf2);
         src = sp<Cand>(g.s_buf);
       }
-      if (k > 0) {
-        Cand* res = nullptr;
-        CU(launch_sort_cands(src, sp<Cand>(g.s_buf2), sp<int>(g.s_grp), m, st, &res,
-                             &t_stats.launches));
-        const u64 keepn = std::min<u64>(m, (u64)k);
-        if (res != src) CU(cudaMemcpyAsync(src, res, sizeof(Cand) * keepn, cudaMemcpyDeviceToDevice, st));
-        if (m >= (u64)k) {
-          CU(launch_set_thresh(src, (u64)k, d_th, st));
-          t_stats.launches++;
-        }
-        kept = keepn;
+      if (k > 0 && m >= (u64)k) {
+        u64 kk = 0;
+        CU(select_best(g, measure, m, (u64)k, &kk, /*sorted=*/false));
+        // s_buf now holds the best k (exact measures: unordered, the worst of
+        // them is the threshold; SC / LHN: sorted, entry k-1 is)
+        if (measure == LP_SC || measure == LP_LHN) CU(launch_set_thresh(sp<Cand>(g.s_buf), (u64)k, d_th, st));
+        else CU(launch_thresh_worst(sp<Cand>(g.s_buf), (u64)k, misc_worst(g), d_th, st, &t_stats.launches));
+        kept = (u64)k;
       } else {
         kept = m;
       }
       // guarantee room for progress
-      const bool progress = (done_w + done_c) > h.nfailed;
+      const bool progress = (done[0] + done[1] + done[2]) > h.nfailed;
       if (k == 0 || !progress || C - kept < (C >> 2)) {
         const u64 C2 = C * 2;
         CU(ensure(g, g.s_buf2, sizeof(Cand) * C2));
@@ -598,34 +698,27 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
         CU(cudaStreamSynchronize(st));
         std::swap(g.s_buf, g.s_buf2);
         CU(ensure(g, g.s_buf2, sizeof(Cand) * C2));
+        CU(ensure(g, g.s_buf3, sizeof(Cand) * C2));
         CU(ensure(g, g.s_grp, sizeof(int) * sort_splits_needed(C2)));
         C = C2;
       }
     } else {
       kept = valid;
     }
-    // next queues: failed records, split halves, then what was never claimed
-    headw.clear();
-    headc.clear();
-    for (const int4& r : failed) {
-      if (r.w & (1 << 30)) headw.push_back(r);
-      else headc.push_back(r);
-    }
-    for (const int4& r : splits) split_item(r, dense_span, headc);
-    u64 nw2 = 0, nc2 = 0;
-    CU(build_queue(g, *wq2, headw, sp<int4>(*wq), done_w, nw, &nw2));
-    CU(build_queue(g, *cq2, headc, sp<int4>(*cq), done_c, nc, &nc2));
-    std::swap(wq, wq2);
-    std::swap(cq, cq2);
-    nw = nw2;
-    nc = nc2;
+    for (auto& hd : heads) hd.clear();
+    for (const int4& r : failed) heads[record_tier(r)].push_back(r);
+    for (const int4& r : splits) split_item(r, A.big_span, heads[2]);
+    CU(rebuild_queues(g, Q, heads, done));
   }
   tm.mark(2);
-  // final selection
-  Cand* src = sp<Cand>(g.s_buf);
-  Cand* res = src;
-  CU(launch_sort_cands(src, sp<Cand>(g.s_buf2), sp<int>(g.s_grp), kept, st, &res,
-                       &t_stats.launches));
+  // final selection: the best k, sorted
+  u64 nsorted = kept;
+  if (k > 0 && kept > (u64)k) CU(select_best(g, measure, kept, (u64)k, &nsorted, /*sorted=*/true));
+  Cand* res = sp<Cand>(g.s_buf);
+  if (!(k > 0 && kept > (u64)k)) {
+    CU(launch_sort_cands(res, sp<Cand>(g.s_buf2), sp<int>(g.s_grp), kept, st, &res,
+                         &t_stats.launches));
+  }
   const u64 found = k > 0 ? std::min<u64>(kept, (u64)k) : kept;
   *out_n = (int64_t)found;
   t_stats.admitted = (int64_t)kept;
@@ -641,7 +734,7 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
     CU(launch_emit_global(res, nwrite, measure, g.fixbits, d_links, st));
     t_stats.launches++;
     if (measure == LP_AA || measure == LP_RA) {
-      CU(launch_pair_cn(d_links, nullptr, 1, nwrite, g.d_off, g.d_idx, g.d_deg, A.cap, st));
+      CU(launch_pair_cn(d_links, nullptr, 1, nwrite, g.d_off, g.d_idx, g.d_deg, g.d_arc, A.cap, st));
       t_stats.launches++;
     }
     if (!out_dev)
@@ -679,52 +772,32 @@ static lp_status predict_sources(Graph& g, int measure, int cap, const int* d_sr
     CU(cudaStreamSynchronize(st));
     if (bad) return fail(LP_EINVAL, "lp_predict_sources: source id out of range");
   }
-  const int32_t zero = 0;
-  (void)zero;
   CU(cudaMemsetAsync(d_counts, 0, sizeof(int) * (size_t)n_src, st));
   if (cap == 0 || g.n == 0) {
     CU(cudaStreamSynchronize(st));
     return LP_OK;
   }
-  ScanArgs A = base_args(g, measure, cap, threshold, 1);
-  const int dense_span = (measure == LP_AA || measure == LP_RA) ? kCtaSmem / 8 : kCtaSmem / 4;
+  ScanArgs A = base_args(g, measure, cap, threshold, 1, k);
   A.sources = d_src;
-  A.k = k;
-  CU(ensure(g, g.s_warpq, sizeof(int4) * ((size_t)n_src + 1)));
   CU(ensure(g, g.s_top, sizeof(TopEnt) * (size_t)n_src * k));
   CU(ensure(g, g.s_grp, sizeof(int2) * ((size_t)n_src + 1)));
   CU(ensure(g, g.s_split, sizeof(int4) * (1 << 20)));
-  u64 itemq_cap = std::max<u64>(1024, g.s_itemq.bytes / sizeof(int4));
-  CU(ensure(g, g.s_itemq, sizeof(int4) * itemq_cap));
   A.out_top = sp<TopEnt>(g.s_top);
   A.out_cnt = d_counts;
   Counters h{};
-  for (int attempt = 0; attempt < 3; ++attempt) {
-    CU(cudaMemsetAsync(d_ctr, 0, sizeof(Counters), st));
-    A.ctr = d_ctr;
-    CU(launch_estimate(A, n_src, sp<int4>(g.s_warpq), sp<int4>(g.s_itemq), itemq_cap,
-                       sp<int2>(g.s_grp), st));
-    t_stats.launches++;
-    CU(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    if (h.nitem <= itemq_cap) break;
-    itemq_cap = h.nitem + 1024;
-    CU(ensure(g, g.s_itemq, sizeof(int4) * itemq_cap));
-  }
-  if (h.nitem > itemq_cap) return fail(LP_EINTERNAL, "lp_predict_sources: item queue sizing");
-  estimate_stats(h);
+  lp_status s = run_estimate(g, A, n_src, sp<int2>(g.s_grp), h);
+  if (s != LP_OK) return s;
   tm.mark(1);
   // partial lists: one per non-single item, including split halves
   u64 partial_cap = h.nitem + 16;
   CU(ensure(g, g.s_partial, sizeof(TopEnt) * partial_cap * k));
   CU(ensure(g, g.s_phdr, sizeof(int2) * partial_cap));
-  Graph::Scratch* cq = &g.s_itemq;
-  Graph::Scratch* cq2 = &g.s_itemq2;
-  u64 nw = h.nwarp, nc = h.nitem;
+  Queues Q = {{&g.s_warpq, &g.s_medq, &g.s_itemq}, {&g.s_warpq2, &g.s_medq2, &g.s_itemq2},
+              {h.nwarp, h.nmed, h.nitem}};
   u64 npartial = 0;
-  std::vector<int4> splits, headc;
-  const std::vector<int4> none;
-  for (int round = 0; nw + nc > 0; ++round) {
+  std::vector<int4> splits;
+  std::vector<int4> heads[3];
+  for (int round = 0; Q.n[0] + Q.n[1] + Q.n[2] > 0; ++round) {
     if (round > 10000) return fail(LP_EINTERNAL, "lp_predict_sources: no progress");
     Counters z{};
     z.npartial = npartial;
@@ -735,11 +808,12 @@ static lp_status predict_sources(Graph& g, int measure, int cap, const int* d_sr
     A.partial = sp<TopEnt>(g.s_partial);
     A.partial_hdr = sp<int2>(g.s_phdr);
     A.partial_cap = partial_cap;
-    CU(scan_launches(g, A, sp<int4>(g.s_warpq), nw, sp<int4>(*cq), nc, tm.on));
-    t_stats.launches += (nw > 0) + (nc > 0);
+    A.prof = options_snapshot().phase_profile ? d_ctr->prof : nullptr;
+    CU(scan_launches(g, A, Q, tm.on));
     CU(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    scan_times(g, nw, nc, tm.on);
+    scan_times(g, Q, tm.on);
+    for (int i = 0; i < 6; ++i) t_stats.phase_cycles[i] += (int64_t)h.prof[i];
     if (h.error) return fail(LP_EINTERNAL, "lp_predict_sources: device check %u", h.error);
     t_stats.candidates += (int64_t)h.candidates;
     t_stats.splits += (int32_t)h.nsplit;
@@ -747,17 +821,14 @@ static lp_status predict_sources(Graph& g, int measure, int cap, const int* d_sr
     splits.resize(h.nsplit);
     if (h.nsplit)
       CU(cudaMemcpy(splits.data(), g.s_split.p, sizeof(int4) * h.nsplit, cudaMemcpyDeviceToHost));
-    headc.clear();
-    for (const int4& r : splits) split_item(r, dense_span, headc);
-    for (int4& r : headc) r.w &= ~kItemSingle;
-    nw = 0;
-    u64 nc2 = 0;
-    CU(build_queue(g, *cq2, headc, sp<int4>(*cq), nc, nc, &nc2));
-    std::swap(cq, cq2);
-    nc = nc2;
-    if (npartial + nc + 16 > partial_cap) {
+    for (auto& hd : heads) hd.clear();
+    for (const int4& r : splits) split_item(r, A.big_span, heads[2]);
+    for (int4& r : heads[2]) r.w &= ~kItemSingle;
+    const u64 done[3] = {Q.n[0], Q.n[1], Q.n[2]};  // no buffer: everything claimed ran
+    CU(rebuild_queues(g, Q, heads, done));
+    if (npartial + Q.n[2] + 16 > partial_cap) {
       // grow the partial store, keeping what is there
-      const u64 cap2 = (npartial + nc) * 2 + 16;
+      const u64 cap2 = (npartial + Q.n[2]) * 2 + 16;
       Graph::Scratch np, nh;
       CU(cudaMalloc(&np.p, sizeof(TopEnt) * cap2 * k));
       np.bytes = sizeof(TopEnt) * cap2 * k;
@@ -806,7 +877,7 @@ static lp_status predict_sources(Graph& g, int measure, int cap, const int* d_sr
                          st));
   t_stats.launches++;
   if (measure == LP_AA || measure == LP_RA) {
-    CU(launch_pair_cn(d_out, d_counts, k, (u64)n_src * k, g.d_off, g.d_idx, g.d_deg, A.cap, st));
+    CU(launch_pair_cn(d_out, d_counts, k, (u64)n_src * k, g.d_off, g.d_idx, g.d_deg, g.d_arc, A.cap, st));
     t_stats.launches++;
   }
   tm.mark(3);

@@ -15,16 +15,22 @@ namespace lp {
 typedef unsigned long long u64;
 typedef unsigned int u32;
 
-constexpr int kEmpty = -1;               // empty hash key
-constexpr int kWarpSlots = 1024;         // per-warp hash table (warp tier)
-constexpr int kWarpMaxWedges = 512;      // warp tier: W(a) <= this
-constexpr int kCtaThreads = 512;         // CTA items
+constexpr int kEmpty = 0;                // empty hash key (keys are stored as c + 1)
+constexpr int kWarpSlots = 512;          // per-warp hash table (warp tier)
+constexpr int kWarpMaxWedges = 256;      // warp tier: W(a) <= this
+constexpr int kWarpTierThreads = 256;
+constexpr int kMedThreads = 128;         // medium tier: one 4-warp CTA per source
+constexpr int kMedSlots = 2048;
+constexpr int kMedMaxWedges = 1024;
+constexpr int kCtaThreads = 1024;        // large tier: one 32-warp CTA per item
 constexpr int kCtaWarps = kCtaThreads / 32;
-constexpr int kCtaSlots = 16384;         // CTA hash table slots
+constexpr int kCtaSlots = 16384;         // largest CTA hash table
 constexpr int kCtaMaxWedges = 8192;      // single-item hash: W <= this
 constexpr int kSplitTarget = 6144;       // wedges per split hash item
-constexpr int kCtaSmem = 192 * 1024;     // dynamic shared memory of a CTA item
-constexpr int kWarpTierThreads = 256;
+constexpr int kCtaSmem = 192 * 1024;     // table bytes of a large-tier CTA
+// shared memory of a large-tier CTA beyond its table: 2048 arc cursors and a
+// queue of 768 long segments (start, length, piece prefix, weight)
+constexpr int kBigExtraSmem = 2048 * 4 + 768 * (4 + 4 + 4 + 8);
 
 // Item kinds (int4.w of a CTA work record).
 constexpr int kItemDense = 1;    // dense counters over [lo, hi)
@@ -60,7 +66,9 @@ struct Counters {
   u64 kept_arcs;
   u64 scanned_arcs;
   u64 nwarp;         // warp queue length written by the estimate kernel
-  u64 nitem;         // CTA item queue length written by the estimate kernel
+  u64 nitem;         // large-tier item queue length written by the estimate kernel
+  u64 nmed;          // medium queue length
+  u64 claim_m;
   u64 claim_w;       // dynamic claim counters
   u64 claim_c;
   u64 cand_cnt;      // selection buffer fill (may exceed capacity)
@@ -69,9 +77,10 @@ struct Counters {
   u64 nsplit;        // overflowed hash items
   u64 npartial;      // per-source partial lists written
   u64 dense_items;
-  u64 tier_wedges[2];
-  u64 tier_arcs[2];
-  u64 tier_kept[2];
+  u64 tier_wedges[3];
+  u64 tier_arcs[3];
+  u64 tier_kept[3];
+  u64 prof[6];
   u32 full;          // selection buffer full
   u32 error;         // device consistency error code
   u64 pad[2];
@@ -110,18 +119,27 @@ struct ScanArgs {
   u64 partial_cap;
   // binning parameters
   int warp_max;        // warp tier: W <= warp_max (<= kWarpMaxWedges)
-  int cta_max;         // single CTA item: W <= cta_max (<= kCtaMaxWedges)
+  int med_max;         // medium tier: W <= med_max (<= kMedMaxWedges)
+  int cta_max;         // single large item: W <= cta_max (<= 2^(big_logcap-1))
   int split_target;    // wedges per split hash item
-  int split_logcap;    // log2 slots of split hash items (<= log2 kCtaSlots)
+  int split_logcap;    // log2 slots of split hash items (<= big_logcap)
+  int big_logcap;      // log2 hash slots that fit the large-tier table bytes
+  int big_span;        // dense window of a large-tier item (vertices)
+  int big_bytes;       // table bytes of a large-tier CTA
+  int item_wedges;     // target wedges of one dense sweep item
+  u64* prof;           // optional: large-tier phase cycles (6 entries) or null
 };
 
 // Process-wide tuning options (lp_set_option).
 struct Options {
   long long select_buffer = 8ll << 20;
   int warp_max = kWarpMaxWedges;
+  int med_max = kMedMaxWedges;
   int cta_max = kCtaMaxWedges;
   int split_target = kSplitTarget;
   int split_logcap = 14;
+  long long item_wedges = 1 << 18;
+  int phase_profile = 0;
 };
 Options options_snapshot();
 
@@ -143,10 +161,11 @@ struct Graph {
     void* p = nullptr;
     size_t bytes = 0;
   };
-  Scratch s_ctr, s_w, s_warpq, s_itemq, s_warpq2, s_itemq2, s_buf, s_buf2, s_failed, s_split,
-      s_thresh, s_flags, s_partial, s_phdr, s_top, s_cnt, s_links, s_src, s_grp;
+  Scratch s_ctr, s_w, s_warpq, s_itemq, s_warpq2, s_itemq2, s_medq, s_medq2, s_buf, s_buf2,
+      s_failed, s_split, s_thresh, s_flags, s_partial, s_phdr, s_top, s_cnt, s_links, s_src, s_grp,
+      s_buf3, s_misc;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};  // per-kernel timing
+  cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // per kernel
 };
 
 // ---------------------------------------------------------------- device --
@@ -176,10 +195,11 @@ inline u64 sort_splits_needed(u64 n) { return n / 2048 + 2; }
 cudaError_t launch_sort_cands(Cand* d_a, Cand* d_tmp, int* splits, u64 n, cudaStream_t st,
                               Cand** result, int* launches);
 cudaError_t launch_set_thresh(const Cand* sorted, u64 k, Thresh* t, cudaStream_t st);
-cudaError_t launch_estimate(const ScanArgs& A, int n_rec, int4* warpq, int4* itemq, u64 itemq_cap,
-                            int2* grp, cudaStream_t st);
 cudaError_t launch_scan_warp(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
 cudaError_t launch_scan_cta(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
+cudaError_t launch_scan_med(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
+cudaError_t launch_estimate2(const ScanArgs& A, int n_rec, int4* warpq, int4* medq, int4* itemq,
+                             u64 itemq_cap, int2* grp, cudaStream_t st);
 cudaError_t launch_merge_partials(const int4* grp_list, int ngrp, const int* order,
                                   const TopEnt* partial, const int2* hdr, int k, TopEnt* out_top,
                                   int* out_cnt, cudaStream_t st);
@@ -188,7 +208,14 @@ cudaError_t launch_emit_global(const Cand* c, u64 n, int measure, int fixbits, l
 cudaError_t launch_emit_sources(const TopEnt* top, const int* cnt, const int* sources, int n_src,
                                 int k, int measure, int fixbits, lp_link* out, cudaStream_t st);
 cudaError_t launch_pair_cn(lp_link* links, const int* cnt_rows, int k, u64 n, const int* off,
-                           const int* idx, const int* deg, int cap, cudaStream_t st);
+                           const int* idx, const int* deg, const Arc* arc, int cap,
+                           cudaStream_t st);
+constexpr int kRadixBinsHost = 2048;
+cudaError_t radix_select(const Cand* src, u64 n, u64 k, int measure, Cand* sel, Cand* actA,
+                         Cand* actB, u32* d_hist, u64* d_cnt, cudaStream_t st, u64* out_n,
+                         int* launches);
+cudaError_t launch_thresh_worst(const Cand* a, u64 n, Cand* tmp, Thresh* t, cudaStream_t st,
+                                int* launches);
 cudaError_t launch_filter_failed(Cand* d_buf, u64 n, const unsigned char* d_flag,
                                  const int4* d_failed_sorted, int nfailed, Cand* d_out,
                                  Counters* d_ctr, u64* d_count, cudaStream_t st);

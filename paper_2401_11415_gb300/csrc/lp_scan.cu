@@ -8,26 +8,32 @@
 // and hands the pair to the selection (Section 4.1.6).
 //
 // GPU design (replaces the paper's OpenMP loop with per-thread dense tables):
-//  * k_estimate: one warp per source computes the exact wedge count W(a)
-//    from the per-arc table (hub arcs contribute nothing and their adjacency
-//    lists are never read) and bins the source:
-//      - W <= 512: warp tier, a per-warp open-addressing table in shared
-//        memory sized 2W..4W slots;
-//      - W <= 8192: one CTA item over the whole vertex range;
-//      - larger: the c-range is cut into items; each item is a CTA with either
-//        a shared-memory hash (split by vertex id, binary search per arc for
-//        the sub-range) or a dense shared-memory counter array over an id
-//        window (hubs whose second-order set is a large part of the graph).
-//  * k_scan_warp / k_scan_cta: the wedge loop is flattened per warp: 32 arcs
-//    are loaded (one int4 per lane), their suffix lengths prefix-summed with
-//    shuffles, and the warp walks the concatenated suffixes 32 wedges at a
-//    time, so every lane reads one coalesced neighbour id per step whatever
-//    the intermediary degrees are.
-//  * Counts are u32 (CN family).  AA and RA accumulate u64 fixed-point
-//    weights round(2^F / ln|Gamma_b|) and round(2^F / |Gamma_b|): integer
-//    addition is associative, so results do not depend on thread order.
+//  * k_estimate: 32 sources per warp (one per lane; sources of high degree
+//    are summed by the whole warp) compute the exact wedge count W(a) from
+//    the per-arc table -- hub arcs add nothing and their adjacency lists are
+//    never read -- and bin each source:
+//      - W <= 256: warp tier, a per-warp shared-memory table of 2W..4W slots;
+//      - W <= 1024: medium tier, one 4-warp CTA with a 2048-slot table;
+//      - W <= 8192: one 32-warp CTA item over the whole vertex range;
+//      - larger: the c-range is cut into items; each item is a 32-warp CTA
+//        with either a shared-memory hash (split by vertex id, a binary search
+//        per arc finds the sub-range) or dense shared-memory counters over an
+//        id window (hubs whose second-order set is a large part of the graph).
+//    Queue appends and statistics are aggregated per warp.
+//  * Wedge loops: a warp holds 32 arcs (one int4 per lane).  Suffixes of 64
+//    or more ids are streamed by the whole warp with four loads in flight per
+//    lane; the short ones are concatenated (prefix sum over the lanes) and
+//    walked 32 wedges at a time, two windows per step, so every lane issues
+//    coalesced reads whatever the intermediary degrees are.
+//  * Tables hold key c + 1 (0 = empty) and are left all-zero after each
+//    source, so no table is cleared before use.  Counts are u32 (CN family);
+//    AA and RA accumulate u64 fixed-point weights round(2^F / ln|Gamma_b|)
+//    and round(2^F / |Gamma_b|): integer addition is associative, so the
+//    sums do not depend on thread order.
 #include <float.h>
 #include <math.h>
+
+#include <type_traits>
 
 #include "lp_internal.cuh"
 
@@ -35,8 +41,8 @@ namespace lp {
 
 #define FULLMASK 0xffffffffu
 
-__device__ __forceinline__ u32 hash_slot(int c, int logcap) {
-  return ((u32)c * 0x9E3779B1u) >> (32 - logcap);
+__device__ __forceinline__ u32 hash_slot(int key, int logcap) {
+  return ((u32)key * 0x9E3779B1u) >> (32 - logcap);
 }
 
 __host__ __device__ __forceinline__ int ceil_log2(u64 x) {
@@ -86,125 +92,199 @@ __device__ __forceinline__ double key_value(int measure, u64 num, u64 den, u64 c
 
 // --------------------------------------------------------------- estimate --
 
-// Per record r (global mode: source r; per-source mode: sources[r]): exact
-// wedge count and binning.  Warp records: {r, lo, hi, W | 1<<30}.  CTA items:
+struct TierStats {
+  u64 w[3], a[3], k[3];
+  u64 dense;
+};
+
+// Per record r (global mode: source r; per-source mode: sources[r]).
+// Warp records: {r, lo, hi, W | 1<<30}.  Medium and large items:
 // {r, lo, hi, kind | logcap << 8}.  grp[r] = (first item, item count) in the
 // per-source mode.
 template <int MODE, bool V64>
-__global__ void k_estimate(ScanArgs A, int n_rec, int4* __restrict__ warpq,
-                           int4* __restrict__ itemq, u64 itemq_cap, int2* __restrict__ grp) {
+__global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* __restrict__ warpq,
+                                                  int4* __restrict__ medq,
+                                                  int4* __restrict__ itemq, u64 itemq_cap,
+                                                  int2* __restrict__ grp) {
   const int lane = lane_id();
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int dense_span = (V64 ? kCtaSmem / 8 : kCtaSmem / 4);
-  for (int r = warp; r < n_rec; r += nwarps) {
-    const int a = MODE ? A.sources[r] : r;
-    const int e0 = A.off[a], e1 = A.off[a + 1];
+  const u32 lt = (1u << lane) - 1u;
+  TierStats ts;
+  for (int i = 0; i < 3; ++i) ts.w[i] = ts.a[i] = ts.k[i] = 0;
+  ts.dense = 0;
+  for (int base = gwarp * 32; base < n_rec; base += nwarps * 32) {
+    const int r = base + lane;
+    const bool valid = r < n_rec;
+    int a = 0, e0 = 0, e1 = 0;
+    if (valid) {
+      a = MODE ? A.sources[r] : r;
+      e0 = A.off[a];
+      e1 = A.off[a + 1];
+    }
     u64 W = 0;
     u32 kept = 0;
-    for (int e = e0 + lane; e < e1; e += 32) {
-      const Arc t = A.arc[e];
-      if (t.z <= A.cap) {
-        W += MODE ? (u64)(t.z - 1) : (u64)(t.y - t.x - 1);
-        ++kept;
+    const bool small = valid && (e1 - e0) <= 64;
+    if (small) {
+      for (int e = e0; e < e1; ++e) {
+        const Arc t = A.arc[e];
+        if (t.z <= A.cap) {
+          W += MODE ? (u64)(t.z - 1) : (u64)(t.y - t.x - 1);
+          ++kept;
+        }
       }
     }
+    u32 big = __ballot_sync(FULLMASK, valid && !small);
+    while (big) {
+      const int j = __ffs(big) - 1;
+      big &= big - 1;
+      const int j0 = __shfl_sync(FULLMASK, e0, j), j1 = __shfl_sync(FULLMASK, e1, j);
+      u64 Wj = 0;
+      u32 kj = 0;
+      for (int e = j0 + lane; e < j1; e += 32) {
+        const Arc t = A.arc[e];
+        if (t.z <= A.cap) {
+          Wj += MODE ? (u64)(t.z - 1) : (u64)(t.y - t.x - 1);
+          ++kj;
+        }
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      W += __shfl_xor_sync(FULLMASK, W, o);
-      kept += __shfl_xor_sync(FULLMASK, kept, o);
+      for (int o = 16; o > 0; o >>= 1) {
+        Wj += __shfl_xor_sync(FULLMASK, Wj, o);
+        kj += __shfl_xor_sync(FULLMASK, kj, o);
+      }
+      if (lane == j) {
+        W = Wj;
+        kept = kj;
+      }
     }
-    if (lane != 0) continue;
-    atomicAdd(&A.ctr->wedges, W);
-    atomicAdd(&A.ctr->kept_arcs, (u64)kept);
-    atomicAdd(&A.ctr->scanned_arcs, (u64)(e1 - e0));
+    // binning
     const int lo = MODE ? 0 : a + 1;
     const int hi = A.n;
-    if (MODE) grp[r] = make_int2(-1, 0);
-    if (W == 0) {
-      if (MODE) A.out_cnt[r] = 0;
-      continue;
+    int tier = -1;
+    if (valid && W > 0) tier = W <= (u64)A.warp_max ? 0 : (W <= (u64)A.med_max ? 1 : 2);
+    if (tier >= 0) {
+      ts.w[tier] += W;
+      ts.a[tier] += (u64)(e1 - e0);
+      ts.k[tier] += kept;
     }
-    const int tier = W <= (u64)A.warp_max ? 0 : 1;
-    atomicAdd(&A.ctr->tier_wedges[tier], W);
-    atomicAdd(&A.ctr->tier_arcs[tier], (u64)(e1 - e0));
-    atomicAdd(&A.ctr->tier_kept[tier], (u64)kept);
-    if (tier == 0) {
-      const u64 q = atomicAdd(&A.ctr->nwarp, 1ull);
-      warpq[q] = make_int4(r, lo, hi, (int)W | (1 << 30));
-      continue;
+    if (MODE && valid) {
+      grp[r] = make_int2(-1, 0);
+      if (W == 0) A.out_cnt[r] = 0;
     }
-    int P, kind, logcap;
-    const u64 span = (u64)(hi - lo);
-    if (W <= (u64)A.cta_max) {
-      P = 1;
-      kind = 0;
-      logcap = max(10, ceil_log2(2 * W));
-    } else {
-      const u64 ph = (W + A.split_target - 1) / A.split_target;
-      const u64 pd = (span + dense_span - 1) / dense_span;
-      const double cost_h = (double)ph * kept * 24.0 + (double)W * 4.0;
-      const double cost_d = (double)pd * ((double)kept * 24.0 + dense_span / 4.0) + (double)W;
-      logcap = A.split_logcap;
-      if (cost_d < cost_h) {
-        P = (int)pd;
-        kind = kItemDense;
-      } else {
-        P = (int)min(ph, span);
-        kind = 0;
+    // warp tier
+    {
+      const u32 m = __ballot_sync(FULLMASK, tier == 0);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        u64 q = 0;
+        if (lane == leader) q = atomicAdd(&A.ctr->nwarp, (u64)__popc(m));
+        q = __shfl_sync(FULLMASK, q, leader);
+        if (tier == 0) warpq[q + __popc(m & lt)] = make_int4(r, lo, hi, (int)W | (1 << 30));
       }
     }
-    if (MODE && P == 1) kind |= kItemSingle;
-    const u64 base = atomicAdd(&A.ctr->nitem, (u64)P);
-    if (kind & kItemDense) atomicAdd(&A.ctr->dense_items, (u64)P);
-    if (base + P > itemq_cap) continue;  // host re-runs with a larger queue
-    if (MODE) grp[r] = make_int2((int)base, P);
-    for (int p = 0; p < P; ++p) {
-      int l2, h2;
-      if (kind & kItemDense) {
-        l2 = lo + p * dense_span;
-        h2 = min(hi, l2 + dense_span);
-      } else {
-        l2 = lo + (int)((span * (u64)p) / (u64)P);
-        h2 = lo + (int)((span * (u64)(p + 1)) / (u64)P);
+    // medium tier
+    {
+      const u32 m = __ballot_sync(FULLMASK, tier == 1);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        u64 q = 0;
+        if (lane == leader) q = atomicAdd(&A.ctr->nmed, (u64)__popc(m));
+        q = __shfl_sync(FULLMASK, q, leader);
+        if (tier == 1) {
+          const int logcap = max(6, min(11, ceil_log2(2 * W)));
+          const int kind = MODE ? kItemSingle : 0;
+          medq[q + __popc(m & lt)] = make_int4(r, lo, hi, kind | (logcap << 8) | (1 << 29));
+        }
       }
-      itemq[base + p] = make_int4(r, l2, h2, kind | (logcap << 8));
     }
+    // large tier: P items per source
+    int P = 0, kind = 0, logcap = 0, Gd = 1;
+    if (tier == 2) {
+      const u64 span = (u64)(hi - lo);
+      if (W <= (u64)A.cta_max) {
+        P = 1;
+        logcap = max(10, ceil_log2(2 * W));
+      } else {
+        const u64 sh = (W + A.split_target - 1) / A.split_target;
+        const u64 sd = (span + A.big_span - 1) / A.big_span;
+        const u64 pdi = max((u64)1, min(sd, (W + A.item_wedges - 1) / A.item_wedges));
+        const double cost_h = (double)sh * (kept * 24.0 + (1 << A.split_logcap) / 4.0) + W * 3.0;
+        const double cost_d =
+            (double)sd * (kept * 2.0 + A.big_span / 8.0) + (double)W + (double)pdi * kept * 24.0;
+        logcap = A.split_logcap;
+        if (cost_d < cost_h) {
+          Gd = (int)((sd + pdi - 1) / pdi);
+          P = (int)((sd + Gd - 1) / Gd);
+          kind = kItemDense;
+        } else {
+          P = (int)min(sh, span);
+        }
+      }
+      if (MODE && P == 1) kind |= kItemSingle;
+      if (kind & kItemDense) ts.dense += (u64)P;
+    }
+    int incl = P;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULLMASK, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(FULLMASK, incl, 31);
+    if (total) {
+      u64 q = 0;
+      if (lane == 31) q = atomicAdd(&A.ctr->nitem, (u64)total);
+      q = __shfl_sync(FULLMASK, q, 31);
+      const u64 first = q + (u64)(incl - P);
+      if (P && first + P <= itemq_cap) {  // else the host re-runs with a larger queue
+        if (MODE) grp[r] = make_int2((int)first, P);
+        const u64 span = (u64)(hi - lo);
+        for (int p = 0; p < P; ++p) {
+          int l2, h2;
+          int gcount = 1;
+          if (kind & kItemDense) {
+            l2 = lo + (int)min(span, (u64)p * Gd * A.big_span);
+            h2 = lo + (int)min(span, (u64)(p + 1) * Gd * A.big_span);
+            gcount = (h2 - l2 + A.big_span - 1) / A.big_span;
+          } else {
+            l2 = lo + (int)((span * (u64)p) / (u64)P);
+            h2 = lo + (int)((span * (u64)(p + 1)) / (u64)P);
+          }
+          itemq[first + p] = make_int4(r, l2, h2, kind | (logcap << 8) | ((gcount - 1) << 16));
+        }
+      }
+    }
+  }
+  // statistics, one set of atomics per warp
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ts.w[i] += __shfl_xor_sync(FULLMASK, ts.w[i], o);
+      ts.a[i] += __shfl_xor_sync(FULLMASK, ts.a[i], o);
+      ts.k[i] += __shfl_xor_sync(FULLMASK, ts.k[i], o);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ts.dense += __shfl_xor_sync(FULLMASK, ts.dense, o);
+  if (lane == 0) {
+    u64 w = 0, a = 0, k = 0;
+    for (int i = 0; i < 3; ++i) {
+      if (ts.w[i]) atomicAdd(&A.ctr->tier_wedges[i], ts.w[i]);
+      if (ts.a[i]) atomicAdd(&A.ctr->tier_arcs[i], ts.a[i]);
+      if (ts.k[i]) atomicAdd(&A.ctr->tier_kept[i], ts.k[i]);
+      w += ts.w[i];
+      a += ts.a[i];
+      k += ts.k[i];
+    }
+    if (w) atomicAdd(&A.ctr->wedges, w);
+    if (a) atomicAdd(&A.ctr->scanned_arcs, a);
+    if (k) atomicAdd(&A.ctr->kept_arcs, k);
+    if (ts.dense) atomicAdd(&A.ctr->dense_items, ts.dense);
   }
 }
 
-// ------------------------------------------------------- wedge flattening --
-
-// The warp holds up to 32 arcs (lane j: suffix start s_j, length len_j,
-// weight w_j).  Calls f(c, w) once for each of the sum(len) wedges, lane p
-// of window `base` taking wedge base + p, so neighbour ids are read with
-// consecutive addresses inside each suffix.
-template <typename V, typename F>
-__device__ __forceinline__ void flat_scan(int s, int len, V w, const int* __restrict__ idx,
-                                          F&& f) {
-  const int lane = lane_id();
-  int incl = len;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(FULLMASK, incl, o);
-    if (lane >= o) incl += t;
-  }
-  const int total = __shfl_sync(FULLMASK, incl, 31);
-  const int excl = incl - len;
-  for (int base = 0; base < total; base += 32) {
-    const int p = base + lane;
-    int j = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const int ej = __shfl_sync(FULLMASK, excl, j + step);
-      if (ej <= p) j += step;
-    }
-    const int sj = __shfl_sync(FULLMASK, s, j);
-    const int ej = __shfl_sync(FULLMASK, excl, j);
-    const V wj = __shfl_sync(FULLMASK, w, j);
-    if (p < total) f(__ldg(idx + sj + (p - ej)), wj);
-  }
-}
+// ------------------------------------------------------- wedge loops ------
 
 // First index in idx[l, r) whose value is >= key (lists are sorted).
 __device__ __forceinline__ int lower_bound_g(const int* __restrict__ idx, int l, int r, int key) {
@@ -215,23 +295,83 @@ __device__ __forceinline__ int lower_bound_g(const int* __restrict__ idx, int l,
   return l;
 }
 
+constexpr int kLongArc = 64;
+
+// The warp holds up to 32 arcs (lane j: suffix start s_j, length len_j,
+// weight w_j).  Calls f(c, w) once for every one of the sum(len) wedges.
+template <typename V, typename F>
+__device__ __forceinline__ void scan_arcs(int s, int len, V w, const int* __restrict__ idx, F&& f) {
+  const int lane = lane_id();
+  // long suffixes: the whole warp streams one suffix, four loads per lane
+  u32 lm = __ballot_sync(FULLMASK, len >= kLongArc);
+  while (lm) {
+    const int j = __ffs(lm) - 1;
+    lm &= lm - 1;
+    const int sj = __shfl_sync(FULLMASK, s, j);
+    const int lj = __shfl_sync(FULLMASK, len, j);
+    const V wj = __shfl_sync(FULLMASK, w, j);
+    const int* p = idx + sj;
+    int i = lane;
+    for (; i + 96 < lj; i += 128) {
+      const int c0 = __ldg(p + i), c1 = __ldg(p + i + 32), c2 = __ldg(p + i + 64),
+                c3 = __ldg(p + i + 96);
+      f(c0, wj);
+      f(c1, wj);
+      f(c2, wj);
+      f(c3, wj);
+    }
+    for (; i < lj; i += 32) f(__ldg(p + i), wj);
+  }
+  if (len >= kLongArc) len = 0;
+  // short suffixes: concatenated, two 32-wedge windows per step
+  int incl = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(FULLMASK, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int total = __shfl_sync(FULLMASK, incl, 31);
+  const int excl = incl - len;
+  for (int base = 0; base < total; base += 64) {
+    const int p0 = base + lane, p1 = base + 32 + lane;
+    int j0 = 0, j1 = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int e0 = __shfl_sync(FULLMASK, excl, j0 + step);
+      const int e1 = __shfl_sync(FULLMASK, excl, j1 + step);
+      if (e0 <= p0) j0 += step;
+      if (e1 <= p1) j1 += step;
+    }
+    const int s0 = __shfl_sync(FULLMASK, s, j0) - __shfl_sync(FULLMASK, excl, j0);
+    const int s1 = __shfl_sync(FULLMASK, s, j1) - __shfl_sync(FULLMASK, excl, j1);
+    const V w0 = __shfl_sync(FULLMASK, w, j0);
+    const V w1 = __shfl_sync(FULLMASK, w, j1);
+    int c0 = 0, c1 = 0;
+    if (p0 < total) c0 = __ldg(idx + s0 + p0);
+    if (p1 < total) c1 = __ldg(idx + s1 + p1);
+    if (p0 < total) f(c0, w0);
+    if (p1 < total) f(c1, w1);
+  }
+}
+
 // ----------------------------------------------------------- hash tables --
 
-// Add w to key c.  Returns 1 if c was new, 0 if it existed, 2 if the table
-// had no free slot (bounded probe count).
+// Add w to key c (stored as c + 1).  Returns 1 if c was new, 0 if it
+// existed, 2 if the table had no free slot (bounded probe count).
 template <typename V>
 __device__ __forceinline__ int hash_add(int* keys, V* vals, int logcap, int c, V w) {
   const u32 mask = (1u << logcap) - 1u;
-  u32 h = hash_slot(c, logcap);
+  const int key = c + 1;
+  u32 h = hash_slot(key, logcap);
   for (u32 probe = 0; probe <= mask; ++probe) {
     const int k = ((volatile int*)keys)[h];
-    if (k == c) {
+    if (k == key) {
       atomicAdd(&vals[h], w);
       return 0;
     }
     if (k == kEmpty) {
-      const int old = atomicCAS(&keys[h], kEmpty, c);
-      if (old == kEmpty || old == c) {
+      const int old = atomicCAS(&keys[h], kEmpty, key);
+      if (old == kEmpty || old == key) {
         atomicAdd(&vals[h], w);
         return old == kEmpty ? 1 : 0;
       }
@@ -245,10 +385,11 @@ __device__ __forceinline__ int hash_add(int* keys, V* vals, int logcap, int c, V
 template <typename V>
 __device__ __forceinline__ void hash_kill(int* keys, V* vals, int logcap, int b) {
   const u32 mask = (1u << logcap) - 1u;
-  u32 h = hash_slot(b, logcap);
+  const int key = b + 1;
+  u32 h = hash_slot(key, logcap);
   for (u32 probe = 0; probe <= mask; ++probe) {
     const int k = keys[h];
-    if (k == b) {
+    if (k == key) {
       vals[h] = 0;
       return;
     }
@@ -333,6 +474,229 @@ __device__ __forceinline__ void top_offer(TopEnt* top, int& cnt, int k, bool has
   }
 }
 
+// Position of the n-th (0-based) set bit of mask (mask has more than n bits).
+__device__ __forceinline__ int nth_set_bit(u32 mask, int n) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    const int cnt = __popc(mask & ((1u << w) - 1u));
+    if (cnt <= n) {
+      n -= cnt;
+      mask >>= w;
+      pos += w;
+    }
+  }
+  return pos;
+}
+
+// Score the live entries among four table slots per lane (value 0 = empty or
+// dead): the live ones are first gathered across the warp, then scored 32 at
+// a time with every lane busy.  Returns true if the global buffer
+// overflowed.
+template <typename V, int MODE>
+__device__ __forceinline__ bool score_chunk(const ScanArgs& A, const Thresh& T, int a, u64 da,
+                                            const int (&c4)[4], const V (&v4)[4], TopEnt* top,
+                                            int& tcnt, u64& n_cand) {
+  const int lane = lane_id();
+  u32 m[4];
+  int pre[5];
+  pre[0] = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    m[j] = __ballot_sync(FULLMASK, v4[j] != 0);
+    pre[j + 1] = pre[j] + __popc(m[j]);
+  }
+  const int L = pre[4];
+  const bool dc_needed = needs_dc(A.measure);
+  bool fail = false;
+  for (int r0 = 0; r0 < L; r0 += 32) {
+    const int t = r0 + lane;
+    const int j = (t >= pre[1]) + (t >= pre[2]) + (t >= pre[3]);
+    const u32 mj = j == 0 ? m[0] : (j == 1 ? m[1] : (j == 2 ? m[2] : m[3]));
+    const int src = t < L ? nth_set_bit(mj, t - pre[j]) : 0;
+    int c = 0;
+    V v = 0;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int cc = __shfl_sync(FULLMASK, c4[jj], src);
+      const V vv = __shfl_sync(FULLMASK, v4[jj], src);
+      if (jj == j) {
+        c = cc;
+        v = vv;
+      }
+    }
+    const bool live = t < L;
+    u64 num = 0, den = 1;
+    bool pass = false;
+    if (live) {
+      ++n_cand;
+      const u64 dc = dc_needed ? (u64)__ldg(A.deg + c) : 0;
+      make_key(A.measure, (u64)v, da, dc, num, den);
+      pass = !A.thr_check || key_value(A.measure, num, den, (u64)v, A.fixbits) > A.threshold;
+      if (MODE == 0 && pass && T.valid) pass = before(num, den, a, c, T.num, T.den, T.u, T.v);
+    }
+    if (MODE == 0) {
+      fail |= admit_global(A, pass, num, den, a, c);
+    } else {
+      TopEnt x;
+      x.num = num;
+      x.den = den;
+      x.c = c;
+      x.cn = sizeof(V) == 8 ? 0 : (int)v;
+      top_offer(top, tcnt, A.k, pass, x);
+    }
+  }
+  return fail;
+}
+
+// Score one candidate per lane (live: the lane has one) and hand it to the
+// sink; warp-collective.  Returns true if the global buffer overflowed.
+template <typename V, int MODE>
+__device__ __forceinline__ bool score_one(const ScanArgs& A, const Thresh& T, int a, u64 da,
+                                          bool live, int c, V v, TopEnt* top, int& tcnt,
+                                          u64& n_cand) {
+  u64 num = 0, den = 1;
+  bool pass = false;
+  if (live) {
+    ++n_cand;
+    const u64 dc = needs_dc(A.measure) ? (u64)__ldg(A.deg + c) : 0;
+    make_key(A.measure, (u64)v, da, dc, num, den);
+    pass = !A.thr_check || key_value(A.measure, num, den, (u64)v, A.fixbits) > A.threshold;
+    if (MODE == 0 && pass && T.valid) pass = before(num, den, a, c, T.num, T.den, T.u, T.v);
+  }
+  if (MODE == 0) return admit_global(A, pass, num, den, a, c);
+  TopEnt x;
+  x.num = num;
+  x.den = den;
+  x.c = c;
+  x.cn = sizeof(V) == 8 ? 0 : (int)v;
+  top_offer(top, tcnt, A.k, pass, x);
+  return false;
+}
+
+template <typename V>
+__device__ __forceinline__ void load4(const V* p, V (&v)[4]);
+template <typename V>
+__device__ __forceinline__ void zero4(V* p);
+
+// Score the 128-slot hash chunk [base0, base0 + 128) of a table (lane l owns
+// slots 4l..4l+3; slots at or beyond nslots are absent) and leave it empty.
+// The live entries are first packed to the front of the chunk in place, so
+// they are scored 32 at a time with every lane busy.
+template <typename V, int MODE>
+__device__ __forceinline__ bool score_hash_chunk(const ScanArgs& A, const Thresh& T, int a, u64 da,
+                                                 int* keys, V* vals, int base0, int nslots,
+                                                 TopEnt* top, int& tcnt, u64& n_cand) {
+  const int lane = lane_id();
+  const int base = base0 + lane * 4;
+  int4 k4 = make_int4(0, 0, 0, 0);
+  V v4[4] = {0, 0, 0, 0};
+  if (base < nslots) {
+    k4 = *reinterpret_cast<const int4*>(keys + base);
+    load4<V>(vals + base, v4);
+  }
+  const int kk[4] = {k4.x, k4.y, k4.z, k4.w};
+  int nl = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) nl += (v4[j] != 0) ? 1 : 0;
+  int incl = nl;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(FULLMASK, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int L = __shfl_sync(FULLMASK, incl, 31);
+  __syncwarp();
+  if (L > 0) {
+    int pos = base0 + incl - nl;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (v4[j] != 0) {
+        keys[pos] = kk[j];
+        vals[pos] = v4[j];
+        ++pos;
+      }
+  }
+  __syncwarp();
+  bool fail = false;
+  for (int r0 = 0; r0 < L; r0 += 32) {
+    const int t = r0 + lane;
+    const bool live = t < L;
+    const int c = live ? keys[base0 + t] - 1 : 0;
+    const V v = live ? vals[base0 + t] : (V)0;
+    fail |= score_one<V, MODE>(A, T, a, da, live, c, v, top, tcnt, n_cand);
+  }
+  __syncwarp();
+  if (base < nslots) {
+    *reinterpret_cast<int4*>(keys + base) = make_int4(0, 0, 0, 0);
+    zero4<V>(vals + base);
+  }
+  __syncwarp();
+  return fail;
+}
+
+// Score the touched counters of 32 bitmap words [w0, w0 + 32) of a dense
+// window (words at or beyond nwords are absent), clearing counters and bits.
+template <typename V, int MODE>
+__device__ __forceinline__ bool score_dense_words(const ScanArgs& A, const Thresh& T, int a, u64 da,
+                                                  V* dense, u32* bits, int w0, int nwords, int lg,
+                                                  TopEnt* top, int& tcnt, u64& n_cand) {
+  const int lane = lane_id();
+  const int wi = w0 + lane;
+  u32 w = 0;
+  if (wi < nwords) {
+    w = bits[wi];
+    bits[wi] = 0;
+  }
+  const int rounds = (int)__reduce_max_sync(FULLMASK, (u32)__popc(w));
+  bool fail = false;
+  for (int r = 0; r < rounds; ++r) {
+    bool live = false;
+    int c = 0;
+    V v = 0;
+    if (w) {
+      const int bit = __ffs(w) - 1;
+      w &= w - 1;
+      const int i = wi * 32 + bit;
+      v = dense[i];
+      dense[i] = 0;
+      c = lg + i;
+      live = v != 0;  // 0: a first-order neighbour cleared by the exclusion
+    }
+    fail |= score_one<V, MODE>(A, T, a, da, live, c, v, top, tcnt, n_cand);
+  }
+  return fail;
+}
+
+// Vector loads / stores of four consecutive table slots.
+template <typename V>
+__device__ __forceinline__ void load4(const V* p, V (&v)[4]) {
+  if (sizeof(V) == 8) {
+    const ulonglong2 a = reinterpret_cast<const ulonglong2*>(p)[0];
+    const ulonglong2 b = reinterpret_cast<const ulonglong2*>(p)[1];
+    v[0] = (V)a.x;
+    v[1] = (V)a.y;
+    v[2] = (V)b.x;
+    v[3] = (V)b.y;
+  } else {
+    const uint4 a = *reinterpret_cast<const uint4*>(p);
+    v[0] = (V)a.x;
+    v[1] = (V)a.y;
+    v[2] = (V)a.z;
+    v[3] = (V)a.w;
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ void zero4(V* p) {
+  if (sizeof(V) == 8) {
+    reinterpret_cast<ulonglong2*>(p)[0] = make_ulonglong2(0, 0);
+    reinterpret_cast<ulonglong2*>(p)[1] = make_ulonglong2(0, 0);
+  } else {
+    *reinterpret_cast<uint4*>(p) = make_uint4(0, 0, 0, 0);
+  }
+}
+
 // ------------------------------------------------------------ warp tier ---
 
 template <bool V64, int MODE>
@@ -347,31 +711,35 @@ __global__ void __launch_bounds__(kWarpTierThreads) k_scan_warp(ScanArgs A, cons
   V* vals = reinterpret_cast<V*>(smem + (size_t)nw * kWarpSlots * 4) + wid * kWarpSlots;
   TopEnt* top = reinterpret_cast<TopEnt*>(smem + (size_t)nw * kWarpSlots * (4 + sizeof(V))) +
                 wid * (MODE ? A.k : 0);
-  for (int i = lane; i < kWarpSlots; i += 32) {
-    keys[i] = kEmpty;
-    vals[i] = 0;
+  for (int i = lane * 4; i < kWarpSlots; i += 128) {
+    *reinterpret_cast<int4*>(keys + i) = make_int4(0, 0, 0, 0);
+    zero4<V>(vals + i);
   }
   __syncwarp();
   Thresh T;
   if (MODE == 0) T = *A.thresh;
-  const bool dc_needed = needs_dc(A.measure);
   u64 n_cand = 0;
-  for (;;) {
-    u64 qi = 0;
-    if (lane == 0) {
-      if (MODE == 0 && *(volatile u32*)&A.ctr->full) qi = ~0ull;
-      else qi = atomicAdd(&A.ctr->claim_w, 1ull);
-    }
-    qi = __shfl_sync(FULLMASK, qi, 0);
-    if (qi >= nq) break;
+  // claims with one record of look-ahead; a claimed record is always
+  // processed (once the buffer is full it fails and is re-queued)
+  u64 next = 0;
+  if (lane == 0) {
+    if (MODE == 0 && *(volatile u32*)&A.ctr->full) next = ~0ull;
+    else next = atomicAdd(&A.ctr->claim_w, 1ull);
+  }
+  next = __shfl_sync(FULLMASK, next, 0);
+  while (next < nq) {
+    const u64 qi = next;
     const int4 rec = q[qi];
+    if (lane == 0) {
+      if (MODE == 0 && *(volatile u32*)&A.ctr->full) next = ~0ull;
+      else next = atomicAdd(&A.ctr->claim_w, 1ull);
+    }
     const int r = rec.x;
     const int a = MODE ? A.sources[r] : r;
     const int W = rec.w & 0xffff;
-    const int logcap = max(5, ceil_log2(2 * (u64)W));
+    const int logcap = max(7, ceil_log2(2 * (u64)W));
     const int nslots = 1 << logcap;
     const int e0 = A.off[a], e1 = A.off[a + 1];
-    // scan
     for (int eb = e0; eb < e1; eb += 32) {
       const int e = eb + lane;
       int s = 0, len = 0;
@@ -389,50 +757,24 @@ __global__ void __launch_bounds__(kWarpTierThreads) k_scan_warp(ScanArgs A, cons
           if (len > 0) w = arc_weight<V>(A.measure, t.z, A.fixbits);
         }
       }
-      flat_scan<V>(s, len, w, A.idx, [&](int c, V wc) {
+      scan_arcs<V>(s, len, w, A.idx, [&](int c, V wc) {
         if (MODE == 1 && c == a) return;
         hash_add<V>(keys, vals, logcap, c, wc);
       });
     }
     __syncwarp();
-    // drop first-order neighbours
     for (int e = e0 + lane; e < e1; e += 32) {
       const int b = __ldg(A.idx + e);
       if (MODE == 1 || b > a) hash_kill<V>(keys, vals, logcap, b);
     }
     __syncwarp();
-    // score and select
     const u64 da = (u64)(e1 - e0);
     bool fail = false;
     int tcnt = 0;
-    for (int base = 0; base < nslots; base += 32) {
-      const int slot = base + lane;
-      const int c = keys[slot];
-      const V v = vals[slot];
-      keys[slot] = kEmpty;
-      vals[slot] = 0;
-      const bool live = (c != kEmpty) && (v != 0);
-      u64 num = 0, den = 1;
-      bool pass = false;
-      if (live) {
-        ++n_cand;
-        const u64 dc = dc_needed ? (u64)__ldg(A.deg + c) : 0;
-        make_key(A.measure, (u64)v, da, dc, num, den);
-        pass = !A.thr_check || key_value(A.measure, num, den, (u64)v, A.fixbits) > A.threshold;
-        if (MODE == 0 && pass && T.valid) pass = before(num, den, a, c, T.num, T.den, T.u, T.v);
-      }
-      if (MODE == 0) {
-        fail |= admit_global(A, pass, num, den, a, c);
-      } else {
-        TopEnt x;
-        x.num = num;
-        x.den = den;
-        x.c = c;
-        x.cn = V64 ? 0 : (int)v;
-        top_offer(top, tcnt, A.k, pass, x);
-      }
-    }
+    for (int base0 = 0; base0 < nslots; base0 += 128)
+      fail |= score_hash_chunk<V, MODE>(A, T, a, da, keys, vals, base0, nslots, top, tcnt, n_cand);
     __syncwarp();
+    next = __shfl_sync(FULLMASK, next, 0);
     if (MODE == 0) {
       if (fail && lane == 0) {
         A.ctr->full = 1u;
@@ -446,7 +788,6 @@ __global__ void __launch_bounds__(kWarpTierThreads) k_scan_warp(ScanArgs A, cons
     }
     __syncwarp();
   }
-  // per-warp candidate count
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) n_cand += __shfl_xor_sync(FULLMASK, n_cand, o);
   if (lane == 0 && n_cand) atomicAdd(&A.ctr->candidates, n_cand);
@@ -454,41 +795,54 @@ __global__ void __launch_bounds__(kWarpTierThreads) k_scan_warp(ScanArgs A, cons
 
 // ------------------------------------------------------------- CTA items ---
 
-template <bool V64, int MODE>
-__global__ void __launch_bounds__(kCtaThreads, 1) k_scan_cta(ScanArgs A, const int4* __restrict__ q,
-                                                             u64 nq) {
+// THREADS threads cooperate on one item (medium tier: 128 threads and a
+// 2048-slot table; large tier: 1024 threads, tables and dense windows in
+// table_bytes of shared memory).
+template <bool V64, int MODE, int THREADS>
+__global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 8)) k_scan_cta(ScanArgs A, const int4* __restrict__ q,
+                                                          u64 nq, int table_bytes,
+                                                          u64* __restrict__ claim) {
   typedef typename std::conditional<V64, u64, u32>::type V;
+  constexpr int NW = THREADS / 32;
   extern __shared__ __align__(16) unsigned char smem[];
+  const int max_slots = 1 << (ceil_log2((u64)table_bytes / (4 + sizeof(V)) + 1) - 1);
   int* keys = reinterpret_cast<int*>(smem);
-  V* vals = reinterpret_cast<V*>(smem + kCtaSlots * 4);
+  V* vals = reinterpret_cast<V*>(smem + (size_t)max_slots * 4);
   V* dense = reinterpret_cast<V*>(smem);
-  TopEnt* tops = reinterpret_cast<TopEnt*>(smem + kCtaSmem);
+  TopEnt* tops = reinterpret_cast<TopEnt*>(smem + table_bytes);
   __shared__ int4 s_rec;
-  __shared__ u64 s_qi;
+  __shared__ u64 s_next;
   __shared__ int s_ndistinct;
   __shared__ int s_overflow;
   __shared__ int s_fail;
-  __shared__ int s_tcnt[kCtaWarps];
+  __shared__ int s_tcnt[NW];
 
   const int lane = lane_id();
   const int wid = threadIdx.x >> 5;
+  for (int i = threadIdx.x * 16; i < table_bytes; i += THREADS * 16)
+    *reinterpret_cast<int4*>(smem + i) = make_int4(0, 0, 0, 0);
   Thresh T;
   if (MODE == 0) T = *A.thresh;
-  const bool dc_needed = needs_dc(A.measure);
   u64 n_cand = 0;
+  if (threadIdx.x == 0) {
+    if (MODE == 0 && *(volatile u32*)&A.ctr->full) s_next = ~0ull;
+    else s_next = atomicAdd(claim, 1ull);
+  }
+  __syncthreads();
   for (;;) {
+    const u64 qi = s_next;
+    if (qi >= nq) break;
     if (threadIdx.x == 0) {
-      u64 qi;
-      if (MODE == 0 && *(volatile u32*)&A.ctr->full) qi = ~0ull;
-      else qi = atomicAdd(&A.ctr->claim_c, 1ull);
-      s_qi = qi;
-      if (qi < nq) s_rec = q[qi];
+      s_rec = q[qi];
       s_ndistinct = 0;
       s_overflow = 0;
       s_fail = 0;
     }
     __syncthreads();
-    if (s_qi >= nq) break;
+    if (threadIdx.x == 0) {  // look-ahead claim, read after the item
+      if (MODE == 0 && *(volatile u32*)&A.ctr->full) s_next = ~0ull;
+      else s_next = atomicAdd(claim, 1ull);
+    }
     const int4 rec = s_rec;
     const int r = rec.x;
     const int a = MODE ? A.sources[r] : r;
@@ -499,18 +853,8 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_scan_cta(ScanArgs A, const i
     const int limit = (nslots * 3) / 4;
     const bool full_range = (lo <= (MODE ? 0 : a + 1)) && hi >= A.n;
     const int span = hi - lo;
-    // initialise the table / counters
-    if (is_dense) {
-      for (int i = threadIdx.x; i < span; i += blockDim.x) dense[i] = 0;
-    } else {
-      for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
-        keys[i] = kEmpty;
-        vals[i] = 0;
-      }
-    }
-    __syncthreads();
     const int e0 = A.off[a], e1 = A.off[a + 1];
-    for (int eb = e0 + wid * 32; eb < e1; eb += kCtaWarps * 32) {
+    for (int eb = e0 + wid * 32; eb < e1; eb += NW * 32) {
       const int e = eb + lane;
       int s = 0, len = 0;
       V w = 0;
@@ -535,12 +879,12 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_scan_cta(ScanArgs A, const i
         }
       }
       if (is_dense) {
-        flat_scan<V>(s, len, w, A.idx, [&](int c, V wc) {
+        scan_arcs<V>(s, len, w, A.idx, [&](int c, V wc) {
           if (MODE == 1 && c == a) return;
           atomicAdd(&dense[c - lo], wc);
         });
       } else {
-        flat_scan<V>(s, len, w, A.idx, [&](int c, V wc) {
+        scan_arcs<V>(s, len, w, A.idx, [&](int c, V wc) {
           if (MODE == 1 && c == a) return;
           if (*(volatile int*)&s_overflow) return;
           const int rc = hash_add<V>(keys, vals, logcap, c, wc);
@@ -555,6 +899,11 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_scan_cta(ScanArgs A, const i
     }
     __syncthreads();
     if (!is_dense && s_overflow) {
+      // give the item back for splitting; leave the table empty
+      for (int i = threadIdx.x * 4; i < nslots; i += THREADS * 4) {
+        *reinterpret_cast<int4*>(keys + i) = make_int4(0, 0, 0, 0);
+        zero4<V>(vals + i);
+      }
       if (threadIdx.x == 0) {
         const u64 f = atomicAdd(&A.ctr->nsplit, 1ull);
         if (f < A.split_cap) A.split[f] = rec;
@@ -564,51 +913,34 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_scan_cta(ScanArgs A, const i
       continue;
     }
     // drop first-order neighbours inside [lo, hi)
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    for (int e = e0 + threadIdx.x; e < e1; e += THREADS) {
       const int b = __ldg(A.idx + e);
       if (b < lo || b >= hi || (MODE == 0 && b <= a)) continue;
       if (is_dense) dense[b - lo] = 0;
       else hash_kill<V>(keys, vals, logcap, b);
     }
     __syncthreads();
-    // score and select
+    // score and select: 4 consecutive slots per lane and step
     const u64 da = (u64)(e1 - e0);
-    const int nscan = is_dense ? span : nslots;
-    const int nscan32 = (nscan + 31) & ~31;
+    const int nscan = is_dense ? ((span + 3) & ~3) : nslots;
     bool fail = false;
     TopEnt* top = tops + wid * (MODE ? A.k : 0);
     int tcnt = 0;
-    for (int i = threadIdx.x; i < nscan32; i += blockDim.x) {  // warp-uniform trip count
-      int c = kEmpty;
-      V v = 0;
-      if (i < nscan) {
-        if (is_dense) {
-          v = dense[i];
-          c = lo + i;
-        } else {
-          c = keys[i];
-          v = vals[i];
+    for (int base0 = wid * 128; base0 < nscan; base0 += THREADS * 4) {  // warp-uniform trips
+      if (is_dense) {
+        const int base = base0 + lane * 4;
+        int c4[4] = {0, 0, 0, 0};
+        V v4[4] = {0, 0, 0, 0};
+        if (base < nscan) {
+          load4<V>(dense + base, v4);
+          zero4<V>(dense + base);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) c4[j] = lo + base + j;
         }
-      }
-      const bool live = (c != kEmpty) && (v != 0);
-      u64 num = 0, den = 1;
-      bool pass = false;
-      if (live) {
-        ++n_cand;
-        const u64 dc = dc_needed ? (u64)__ldg(A.deg + c) : 0;
-        make_key(A.measure, (u64)v, da, dc, num, den);
-        pass = !A.thr_check || key_value(A.measure, num, den, (u64)v, A.fixbits) > A.threshold;
-        if (MODE == 0 && pass && T.valid) pass = before(num, den, a, c, T.num, T.den, T.u, T.v);
-      }
-      if (MODE == 0) {
-        fail |= admit_global(A, pass, num, den, a, c);
+        fail |= score_chunk<V, MODE>(A, T, a, da, c4, v4, top, tcnt, n_cand);
       } else {
-        TopEnt x;
-        x.num = num;
-        x.den = den;
-        x.c = c;
-        x.cn = V64 ? 0 : (int)v;
-        top_offer(top, tcnt, A.k, pass, x);
+        fail |= score_hash_chunk<V, MODE>(A, T, a, da, keys, vals, base0, nslots, top, tcnt,
+                                          n_cand);
       }
     }
     if (MODE == 0) {
@@ -625,7 +957,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_scan_cta(ScanArgs A, const i
       __syncthreads();
       if (wid == 0) {
         int cnt = s_tcnt[0];
-        for (int w2 = 1; w2 < kCtaWarps; ++w2) {
+        for (int w2 = 1; w2 < NW; ++w2) {
           const TopEnt* other = tops + w2 * A.k;
           const int oc = s_tcnt[w2];
           for (int j = 0; j < oc; ++j) {
@@ -652,6 +984,406 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_scan_cta(ScanArgs A, const i
     }
     __syncthreads();
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n_cand += __shfl_xor_sync(FULLMASK, n_cand, o);
+  if (lane == 0 && n_cand) atomicAdd(&A.ctr->candidates, n_cand);
+}
+
+// ------------------------------------------------------------ large tier ---
+
+constexpr int kBigCursors = 2048;  // per-arc cursors kept across dense windows
+constexpr int kBigQueue = 768;     // long segments shared by all warps
+constexpr int kLongSeg = 64;       // segments at least this long are shared
+constexpr int kPiece = 256;        // wedges per shared piece
+
+constexpr int kFewArcs = 256;     // up to this many arcs: one arc per warp
+constexpr int kQueueSeg = 256;    // one-arc-per-warp mode: longer segments are shared
+
+// First index in idx[l, r) whose value is >= key; the whole warp searches
+// (32 probes per step, so about log32(r - l) dependent loads).  Warp-uniform
+// arguments; every lane returns the result.
+__device__ __forceinline__ int warp_lower_bound(const int* __restrict__ idx, int l, int r, int key) {
+  const int lane = lane_id();
+  while (r - l > 32) {
+    const int step = (r - l + 31) >> 5;
+    const int p = l + lane * step;
+    const bool lt = p < r && __ldg(idx + p) < key;
+    const int cnt = __popc(__ballot_sync(FULLMASK, lt));
+    if (cnt == 0) return l;
+    const int nl = l + (cnt - 1) * step + 1;
+    const int nr = min(r, l + cnt * step);
+    l = nl;
+    r = nr;
+  }
+  const int p = l + lane;
+  const bool lt = p < r && __ldg(idx + p) < key;
+  return l + __popc(__ballot_sync(FULLMASK, lt));
+}
+
+// The warp streams one segment idx[0, len) with eight loads per lane in
+// flight, calling f(c, w) for each id.
+template <typename V, typename F>
+__device__ __forceinline__ void stream_segment(const int* __restrict__ p, int len, V w, F&& f) {
+  const int lane = lane_id();
+  int i = lane;
+  for (; i + 224 < len; i += 256) {
+    int c[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c[j] = __ldg(p + i + 32 * j);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) f(c[j], w);
+  }
+  for (; i < len; i += 32) f(__ldg(p + i), w);
+}
+
+// First index in idx[l, r) whose value is >= key, searching outward from l.
+__device__ __forceinline__ int lower_bound_gallop(const int* __restrict__ idx, int l, int r,
+                                                  int key) {
+  if (l >= r || __ldg(idx + l) >= key) return l;
+  int prev = l, step = 1;
+  while (true) {
+    const int cur = l + step;
+    if (cur >= r) return lower_bound_g(idx, prev + 1, r, key);
+    if (__ldg(idx + cur) >= key) return lower_bound_g(idx, prev + 1, cur, key);
+    prev = cur;
+    step <<= 1;
+  }
+}
+
+// One 32-warp CTA per item.  A hash item is one vertex range; a dense item
+// sweeps G consecutive windows of at most A.big_span vertices, carrying each
+// arc's position from window to window (no repeated binary search).  In every
+// range, segments of kLongSeg or more wedges are cut into kPiece-wedge pieces
+// that all warps share, so a source with a few long intermediary lists still
+// keeps every warp busy.
+template <bool V64, int MODE>
+__global__ void __launch_bounds__(kCtaThreads, 1) k_scan_big(ScanArgs A, const int4* __restrict__ q,
+                                                             u64 nq, int table_bytes,
+                                                             u64* __restrict__ claim) {
+  typedef typename std::conditional<V64, u64, u32>::type V;
+  constexpr int NW = kCtaThreads / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int max_slots = 1 << (ceil_log2((u64)table_bytes / (4 + sizeof(V)) + 1) - 1);
+  int* keys = reinterpret_cast<int*>(smem);
+  V* vals = reinterpret_cast<V*>(smem + (size_t)max_slots * 4);
+  V* dense = reinterpret_cast<V*>(smem);
+  u32* dbits = reinterpret_cast<u32*>(smem + (size_t)A.big_span * sizeof(V));  // touched bits
+  int* cursors = reinterpret_cast<int*>(smem + table_bytes);
+  int* q_s = cursors + kBigCursors;
+  int* q_len = q_s + kBigQueue;
+  int* q_pref = q_len + kBigQueue;
+  u64* q_w = reinterpret_cast<u64*>(q_pref + kBigQueue);
+  TopEnt* tops = reinterpret_cast<TopEnt*>(q_w + kBigQueue);
+  __shared__ int4 s_rec;
+  __shared__ u64 s_next;
+  __shared__ int s_ndistinct, s_overflow, s_fail, s_qn, s_qpieces, s_qhead;
+  __shared__ int s_tcnt[NW];
+  // optional phase profile (thread 0's clock): 0 item setup, 1 own arcs,
+  // 2 wait for the other warps' arcs, 3 shared pieces, 4 exclusion + scoring,
+  // 5 item end
+  long long t_prof[6] = {0, 0, 0, 0, 0, 0};
+  long long t_last = clock64();
+  const bool prof = A.prof != nullptr && threadIdx.x == 0;
+#define LP_PHASE(i)                        \
+  do {                                     \
+    if (prof) {                            \
+      const long long t_now = clock64();   \
+      t_prof[i] += t_now - t_last;         \
+      t_last = t_now;                      \
+    }                                      \
+  } while (0)
+
+  const int lane = lane_id();
+  const int wid = threadIdx.x >> 5;
+  for (int i = threadIdx.x * 16; i < table_bytes; i += kCtaThreads * 16)
+    *reinterpret_cast<int4*>(smem + i) = make_int4(0, 0, 0, 0);
+  Thresh T;
+  if (MODE == 0) T = *A.thresh;
+  u64 n_cand = 0;
+  if (threadIdx.x == 0) {
+    if (MODE == 0 && *(volatile u32*)&A.ctr->full) s_next = ~0ull;
+    else s_next = atomicAdd(claim, 1ull);
+  }
+  __syncthreads();
+  for (;;) {
+    const u64 qi = s_next;
+    if (qi >= nq) break;
+    if (threadIdx.x == 0) {
+      s_rec = q[qi];
+      s_fail = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // look-ahead claim, read after the item
+      if (MODE == 0 && *(volatile u32*)&A.ctr->full) s_next = ~0ull;
+      else s_next = atomicAdd(claim, 1ull);
+    }
+    const int4 rec = s_rec;
+    const int r = rec.x;
+    const int a = MODE ? A.sources[r] : r;
+    const int lo = rec.y, hi = rec.z;
+    const bool is_dense = (rec.w & kItemDense) != 0;
+    const int logcap = (rec.w >> 8) & 0xff;
+    const int G = is_dense ? ((rec.w >> 16) & 0xfff) + 1 : 1;
+    const int nslots = 1 << logcap;
+    const int limit = (nslots * 3) / 4;
+    const int span = hi - lo;
+    const int e0 = A.off[a], e1 = A.off[a + 1];
+    const bool use_cur = G > 1 && (e1 - e0) <= kBigCursors;
+    const bool few_arcs = (e1 - e0) <= kFewArcs;
+    const u64 da = (u64)(e1 - e0);
+    TopEnt* top = tops + wid * (MODE ? A.k : 0);
+    int tcnt = 0;
+    bool fail = false;
+    bool overflowed = false;
+    for (int g = 0; g < G; ++g) {
+      const int lg = lo + (int)(((u64)span * (u64)g) / (u64)G);
+      const int hg = lo + (int)(((u64)span * (u64)(g + 1)) / (u64)G);
+      const bool full_range = G == 1 && lo <= (MODE ? 0 : a + 1) && hi >= A.n;
+      if (threadIdx.x == 0) {
+        s_ndistinct = 0;
+        s_overflow = 0;
+        s_qn = 0;
+        s_qhead = 0;
+      }
+      __syncthreads();
+      LP_PHASE(0);
+      auto insert = [&](int c, V wc) {
+        if (MODE == 1 && c == a) return;
+        if (is_dense) {
+          const int i = c - lg;
+          if (atomicAdd(&dense[i], wc) == 0) atomicOr(&dbits[i >> 5], 1u << (i & 31));
+        } else {
+          if (*(volatile int*)&s_overflow) return;
+          const int rc = hash_add<V>(keys, vals, logcap, c, wc);
+          if (rc == 1) {
+            if (atomicAdd(&s_ndistinct, 1) >= limit) s_overflow = 1;
+          } else if (rc == 2) {
+            s_overflow = 1;
+          }
+        }
+      };
+      // phase 1 (few arcs): one arc per warp, bounds found by warp-wide
+      // searches, the segment streamed by the warp (the longest are queued)
+      if (few_arcs) {
+        for (int e = e0 + wid; e < e1; e += NW) {
+          const Arc t = A.arc[e];
+          if (t.z > A.cap) continue;  // warp-uniform
+          int s0, s1;
+          if (MODE == 0) {
+            s0 = t.x + 1;
+            s1 = t.y;
+          } else {
+            s0 = t.y - t.z;
+            s1 = t.y;
+          }
+          if (!full_range && s0 < s1) {
+            const int st = (use_cur && g > 0) ? cursors[e - e0] : warp_lower_bound(A.idx, s0, s1, lg);
+            const int en = warp_lower_bound(A.idx, st, s1, hg);
+            if (use_cur && lane == 0) cursors[e - e0] = en;
+            s0 = st;
+            s1 = en;
+          }
+          const int len = s1 - s0;
+          if (len <= 0) continue;
+          const V w = arc_weight<V>(A.measure, t.z, A.fixbits);
+          if (len >= kQueueSeg) {
+            int slot = 0;
+            if (lane == 0) slot = atomicAdd(&s_qn, 1);
+            slot = __shfl_sync(FULLMASK, slot, 0);
+            if (slot < kBigQueue) {
+              if (lane == 0) {
+                q_s[slot] = s0;
+                q_len[slot] = len;
+                q_w[slot] = (u64)w;
+              }
+              continue;
+            }
+          }
+          stream_segment<V>(A.idx + s0, len, w, insert);
+          if (!is_dense && __any_sync(FULLMASK, *(volatile int*)&s_overflow != 0)) break;
+        }
+      }
+      // phase 1 (many arcs): each warp takes 32 arcs at a time; long
+      // segments are queued
+      for (int eb = e0 + wid * 32; !few_arcs && eb < e1; eb += NW * 32) {
+        const int e = eb + lane;
+        int s = 0, len = 0;
+        V w = 0;
+        if (e < e1) {
+          const Arc t = A.arc[e];
+          if (t.z <= A.cap) {
+            int s0, s1;
+            if (MODE == 0) {
+              s0 = t.x + 1;
+              s1 = t.y;
+            } else {
+              s0 = t.y - t.z;
+              s1 = t.y;
+            }
+            if (!full_range && s0 < s1) {
+              const int st = (use_cur && g > 0) ? cursors[e - e0] : lower_bound_g(A.idx, s0, s1, lg);
+              const int en = use_cur ? lower_bound_gallop(A.idx, st, s1, hg)
+                                     : lower_bound_g(A.idx, st, s1, hg);
+              if (use_cur) cursors[e - e0] = en;
+              s0 = st;
+              s1 = en;
+            }
+            s = s0;
+            len = s1 - s0;
+            if (len > 0) w = arc_weight<V>(A.measure, t.z, A.fixbits);
+          }
+        }
+        if (len >= kLongSeg) {
+          const int slot = atomicAdd(&s_qn, 1);
+          if (slot < kBigQueue) {
+            q_s[slot] = s;
+            q_len[slot] = len;
+            q_w[slot] = (u64)w;
+            len = 0;
+          }
+        }
+        scan_arcs<V>(s, len, w, A.idx, insert);
+        if (!is_dense && __any_sync(FULLMASK, *(volatile int*)&s_overflow != 0)) break;
+      }
+      LP_PHASE(1);
+      __syncthreads();
+      LP_PHASE(2);
+      // phase 2: shared pieces of the queued long segments
+      const int nqd = min(s_qn, kBigQueue);
+      if (nqd > 0) {
+        if (wid == 0) {
+          int carry = 0;
+          for (int b0 = 0; b0 < nqd; b0 += 32) {
+            const int i = b0 + lane;
+            const int pc = i < nqd ? (q_len[i] + kPiece - 1) / kPiece : 0;
+            int incl = pc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int t = __shfl_up_sync(FULLMASK, incl, o);
+              if (lane >= o) incl += t;
+            }
+            if (i < nqd) q_pref[i] = carry + incl - pc;
+            carry += __shfl_sync(FULLMASK, incl, 31);
+          }
+          if (lane == 0) s_qpieces = carry;
+        }
+        __syncthreads();
+        const int npieces = s_qpieces;
+        for (;;) {
+          int p = 0;
+          if (lane == 0) p = atomicAdd(&s_qhead, 1);
+          p = __shfl_sync(FULLMASK, p, 0);
+          if (p >= npieces) break;
+          int l2 = 0, h2 = nqd - 1;  // last segment with q_pref <= p
+          while (l2 < h2) {
+            const int m = (l2 + h2 + 1) >> 1;
+            if (q_pref[m] <= p) l2 = m; else h2 = m - 1;
+          }
+          const int off = (p - q_pref[l2]) * kPiece;
+          const int plen = min(kPiece, q_len[l2] - off);
+          const int* src = A.idx + q_s[l2] + off;
+          const V wj = (V)q_w[l2];
+          int i = lane;
+          for (; i + 96 < plen; i += 128) {
+            const int c0 = __ldg(src + i), c1 = __ldg(src + i + 32), c2 = __ldg(src + i + 64),
+                      c3 = __ldg(src + i + 96);
+            insert(c0, wj);
+            insert(c1, wj);
+            insert(c2, wj);
+            insert(c3, wj);
+          }
+          for (; i < plen; i += 32) insert(__ldg(src + i), wj);
+        }
+        __syncthreads();
+      }
+      LP_PHASE(3);
+      if (!is_dense && s_overflow) {
+        // give the range back for splitting; leave the table empty
+        for (int i = threadIdx.x * 4; i < nslots; i += kCtaThreads * 4) {
+          *reinterpret_cast<int4*>(keys + i) = make_int4(0, 0, 0, 0);
+          zero4<V>(vals + i);
+        }
+        overflowed = true;
+        __syncthreads();
+        break;  // hash items have a single range
+      }
+      // drop first-order neighbours inside [lg, hg)
+      for (int e = e0 + threadIdx.x; e < e1; e += kCtaThreads) {
+        const int b = __ldg(A.idx + e);
+        if (b < lg || b >= hg || (MODE == 0 && b <= a)) continue;
+        if (is_dense) dense[b - lg] = 0;
+        else hash_kill<V>(keys, vals, logcap, b);
+      }
+      __syncthreads();
+      // score and select: touched counters (dense) or packed live slots (hash)
+      if (is_dense) {
+        const int nwords = (hg - lg + 31) >> 5;
+        for (int w0 = wid * 32; w0 < nwords; w0 += kCtaThreads)  // warp-uniform trips
+          fail |= score_dense_words<V, MODE>(A, T, a, da, dense, dbits, w0, nwords, lg, top, tcnt,
+                                             n_cand);
+      } else {
+        for (int base0 = wid * 128; base0 < nslots; base0 += kCtaThreads * 4)
+          fail |= score_hash_chunk<V, MODE>(A, T, a, da, keys, vals, base0, nslots, top, tcnt,
+                                            n_cand);
+      }
+      __syncthreads();
+      LP_PHASE(4);
+    }
+    if (overflowed) {
+      if (threadIdx.x == 0) {
+        const u64 f = atomicAdd(&A.ctr->nsplit, 1ull);
+        if (f < A.split_cap) A.split[f] = rec;
+        else A.ctr->error = 2u;
+      }
+      __syncthreads();
+      continue;
+    }
+    if (MODE == 0) {
+      if (fail && lane == 0) s_fail = 1;
+      __syncthreads();
+      if (threadIdx.x == 0 && s_fail) {
+        A.ctr->full = 1u;
+        const u64 f = atomicAdd(&A.ctr->nfailed, 1ull);
+        if (f < A.failed_cap) A.failed[f] = rec;
+        else A.ctr->error = 1u;
+      }
+    } else {
+      if (lane == 0) s_tcnt[wid] = tcnt;
+      __syncthreads();
+      if (wid == 0) {
+        int cnt = s_tcnt[0];
+        for (int w2 = 1; w2 < NW; ++w2) {
+          const TopEnt* other = tops + w2 * A.k;
+          const int oc = s_tcnt[w2];
+          for (int j = 0; j < oc; ++j) {
+            const TopEnt x = other[j];
+            if (cnt >= A.k && !ent_before(x, top[A.k - 1])) break;  // sorted: rest is worse
+            top_insert(top, cnt, A.k, x);
+          }
+        }
+        if (rec.w & kItemSingle) {
+          for (int j = lane; j < cnt; j += 32) A.out_top[(u64)r * A.k + j] = top[j];
+          if (lane == 0) A.out_cnt[r] = cnt;
+        } else {
+          u64 p = 0;
+          if (lane == 0) p = atomicAdd(&A.ctr->npartial, 1ull);
+          p = __shfl_sync(FULLMASK, p, 0);
+          if (p < A.partial_cap) {
+            for (int j = lane; j < cnt; j += 32) A.partial[p * A.k + j] = top[j];
+            if (lane == 0) A.partial_hdr[p] = make_int2(r, cnt);
+          } else if (lane == 0) {
+            A.ctr->error = 3u;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    LP_PHASE(5);
+  }
+#undef LP_PHASE
+  if (prof)
+    for (int i = 0; i < 6; ++i) atomicAdd(&A.prof[i], (u64)t_prof[i]);
+#pragma unroll
   for (int o = 16; o > 0; o >>= 1) n_cand += __shfl_xor_sync(FULLMASK, n_cand, o);
   if (lane == 0 && n_cand) atomicAdd(&A.ctr->candidates, n_cand);
 }
@@ -734,33 +1466,70 @@ __global__ void k_emit_sources(const TopEnt* __restrict__ top, const int* __rest
   const int r = (int)(i / k), j = (int)(i % k);
   if (j >= cnt[r]) return;
   const TopEnt x = top[i];
-  u64 cn = (u64)x.cn;
-  out[i] = make_link(measure, sources[r], x.c, x.num, x.den, cn, fixbits);
+  out[i] = make_link(measure, sources[r], x.c, x.num, x.den, (u64)x.cn, fixbits);
 }
 
 // Common neighbours b of (u, v) with |Gamma_b| <= cap, one warp per link
-// (AA / RA lists, whose tables hold weight sums rather than counts).
+// (AA / RA lists, whose tables hold weight sums rather than counts).  x is
+// the endpoint of smaller degree.  Short Gamma_x (or a much longer Gamma_y):
+// each lane takes elements b of Gamma_x (hub test from the arc table) and
+// looks the other endpoint up in the shorter of Gamma_b and Gamma_y.  Two
+// long lists of similar length: a merge-path intersection across the lanes.
 __global__ void k_pair_cn(lp_link* __restrict__ links, const int* __restrict__ cnt_rows, int k,
                           u64 n, const int* __restrict__ off, const int* __restrict__ idx,
-                          const int* __restrict__ deg, int cap) {
+                          const int* __restrict__ deg, const Arc* __restrict__ arc, int cap) {
   const u64 gw = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = lane_id();
   if (gw >= n) return;
   if (cnt_rows && (int)(gw % k) >= cnt_rows[gw / k]) return;
-  lp_link L = links[gw];
+  const lp_link L = links[gw];
   int x = L.u, y = L.v;
   if (off[x + 1] - off[x] > off[y + 1] - off[y]) {
     const int t = x;
     x = y;
     y = t;
   }
+  const int xs = off[x], xe = off[x + 1];
   const int ys = off[y], ye = off[y + 1];
+  const int dy = ye - ys;
+  const int dx = xe - xs;
   int c = 0;
-  for (int e = off[x] + lane; e < off[x + 1]; e += 32) {
-    const int b = __ldg(idx + e);
-    if (__ldg(deg + b) > cap) continue;
-    const int p = lower_bound_g(idx, ys, ye, b);
-    if (p < ye && __ldg(idx + p) == b) ++c;
+  if (dx <= 64 || dy > 16 * dx || cap <= 4096) {
+    // short Gamma_x or a much longer Gamma_y: look each b of Gamma_x up
+    for (int e = xs + lane; e < xe; e += 32) {
+      const Arc t = arc[e];  // b = t.w, |Gamma_b| = t.z, Gamma_b ends at t.y
+      const int b = t.w, db = t.z;
+      if (db > cap) continue;
+      if (db <= dy) {
+        const int be = t.y, bs = be - db;
+        const int p = lower_bound_g(idx, bs, be, y);
+        c += (p < be && __ldg(idx + p) == y) ? 1 : 0;
+      } else {
+        const int p = lower_bound_g(idx, ys, ye, b);
+        c += (p < ye && __ldg(idx + p) == b) ? 1 : 0;
+      }
+    }
+  } else {
+    // comparable long lists: merge path, each lane merges 1/32 of the
+    // combined length; a match at a lane boundary is counted by the lane
+    // that holds its Gamma_x element (Gamma_x first on ties)
+    const int tot = dx + dy;
+    auto split = [&](int d) {  // elements of Gamma_x among the first d merged
+      int lo = d > dy ? d - dy : 0, hi = d < dx ? d : dx;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(idx + xs + mid) <= __ldg(idx + ys + d - 1 - mid)) lo = mid + 1; else hi = mid;
+      }
+      return lo;
+    };
+    const int d0 = (int)(((long long)tot * lane) / 32), d1 = (int)(((long long)tot * (lane + 1)) / 32);
+    const int i0 = split(d0), i1 = split(d1);
+    int j = d0 - i0;
+    for (int i = i0; i < i1; ++i) {
+      const int xi = __ldg(idx + xs + i);
+      while (j < dy && __ldg(idx + ys + j) < xi) ++j;
+      if (j < dy && __ldg(idx + ys + j) == xi && __ldg(deg + xi) <= cap) ++c;
+    }
   }
   c = __reduce_add_sync(FULLMASK, (u32)c);
   if (lane == 0) links[gw].cn = c;
@@ -779,18 +1548,19 @@ static int num_sms() {
   return g_nsm;
 }
 
-cudaError_t launch_estimate(const ScanArgs& A, int n_rec, int4* warpq, int4* itemq, u64 itemq_cap,
-                            int2* grp, cudaStream_t st) {
+cudaError_t launch_estimate2(const ScanArgs& A, int n_rec, int4* warpq, int4* medq, int4* itemq,
+                             u64 itemq_cap, int2* grp, cudaStream_t st) {
   if (n_rec <= 0) return cudaSuccess;
   const int threads = 256;
-  const int blocks = (int)min((u64)num_sms() * 8, ((u64)n_rec * 32 + threads - 1) / threads);
+  const u64 groups = ((u64)n_rec + 31) / 32;
+  const int blocks = (int)max((u64)1, min((u64)num_sms() * 8, (groups * 32 + threads - 1) / threads));
   const bool v64 = A.measure == LP_AA || A.measure == LP_RA;
   if (A.mode == 0) {
-    if (v64) k_estimate<0, true><<<blocks, threads, 0, st>>>(A, n_rec, warpq, itemq, itemq_cap, grp);
-    else k_estimate<0, false><<<blocks, threads, 0, st>>>(A, n_rec, warpq, itemq, itemq_cap, grp);
+    if (v64) k_estimate<0, true><<<blocks, threads, 0, st>>>(A, n_rec, warpq, medq, itemq, itemq_cap, grp);
+    else k_estimate<0, false><<<blocks, threads, 0, st>>>(A, n_rec, warpq, medq, itemq, itemq_cap, grp);
   } else {
-    if (v64) k_estimate<1, true><<<blocks, threads, 0, st>>>(A, n_rec, warpq, itemq, itemq_cap, grp);
-    else k_estimate<1, false><<<blocks, threads, 0, st>>>(A, n_rec, warpq, itemq, itemq_cap, grp);
+    if (v64) k_estimate<1, true><<<blocks, threads, 0, st>>>(A, n_rec, warpq, medq, itemq, itemq_cap, grp);
+    else k_estimate<1, false><<<blocks, threads, 0, st>>>(A, n_rec, warpq, medq, itemq, itemq_cap, grp);
   }
   return cudaGetLastError();
 }
@@ -821,22 +1591,52 @@ cudaError_t launch_scan_warp(const ScanArgs& A, const int4* q, u64 nq, cudaStrea
   return v64 ? launch_warp_t<true, 1>(A, q, nq, st) : launch_warp_t<false, 1>(A, q, nq, st);
 }
 
+template <bool V64, int MODE, int THREADS>
+static cudaError_t launch_cta_t(const ScanArgs& A, const int4* q, u64 nq, int table_bytes,
+                                u64* claim, cudaStream_t st) {
+  const size_t smem = (size_t)table_bytes + (MODE ? (size_t)(THREADS / 32) * A.k * sizeof(TopEnt) : 0);
+  auto kern = k_scan_cta<V64, MODE, THREADS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int blocks = (int)max((u64)1, min((u64)num_sms() * per_sm, nq));
+  kern<<<blocks, THREADS, smem, st>>>(A, q, nq, table_bytes, claim);
+  return cudaGetLastError();
+}
+
 template <bool V64, int MODE>
-static cudaError_t launch_cta_t(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st) {
-  const size_t smem = (size_t)kCtaSmem + (MODE ? (size_t)kCtaWarps * A.k * sizeof(TopEnt) : 0);
-  auto kern = k_scan_cta<V64, MODE>;
+static cudaError_t launch_big_t(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st) {
+  const int tb = A.big_bytes;
+  const size_t smem = (size_t)tb + kBigExtraSmem +
+                      (MODE ? (size_t)(kCtaThreads / 32) * A.k * sizeof(TopEnt) : 0);
+  auto kern = k_scan_big<V64, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int blocks = (int)max((u64)1, min((u64)num_sms(), nq));
-  kern<<<blocks, kCtaThreads, smem, st>>>(A, q, nq);
+  kern<<<blocks, kCtaThreads, smem, st>>>(A, q, nq, tb, &A.ctr->claim_c);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scan_cta(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st) {
   if (nq == 0) return cudaSuccess;
   const bool v64 = A.measure == LP_AA || A.measure == LP_RA;
-  if (A.mode == 0) return v64 ? launch_cta_t<true, 0>(A, q, nq, st) : launch_cta_t<false, 0>(A, q, nq, st);
-  return v64 ? launch_cta_t<true, 1>(A, q, nq, st) : launch_cta_t<false, 1>(A, q, nq, st);
+  if (A.mode == 0) return v64 ? launch_big_t<true, 0>(A, q, nq, st) : launch_big_t<false, 0>(A, q, nq, st);
+  return v64 ? launch_big_t<true, 1>(A, q, nq, st) : launch_big_t<false, 1>(A, q, nq, st);
+}
+
+cudaError_t launch_scan_med(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st) {
+  if (nq == 0) return cudaSuccess;
+  const bool v64 = A.measure == LP_AA || A.measure == LP_RA;
+  u64* claim = &A.ctr->claim_m;
+  const int tb = kMedSlots * (v64 ? 12 : 8);
+  if (A.mode == 0)
+    return v64 ? launch_cta_t<true, 0, kMedThreads>(A, q, nq, tb, claim, st)
+               : launch_cta_t<false, 0, kMedThreads>(A, q, nq, tb, claim, st);
+  return v64 ? launch_cta_t<true, 1, kMedThreads>(A, q, nq, tb, claim, st)
+             : launch_cta_t<false, 1, kMedThreads>(A, q, nq, tb, claim, st);
 }
 
 cudaError_t launch_merge_partials(const int4* grp_list, int ngrp, const int* order,
@@ -868,11 +1668,12 @@ cudaError_t launch_emit_sources(const TopEnt* top, const int* cnt, const int* so
 }
 
 cudaError_t launch_pair_cn(lp_link* links, const int* cnt_rows, int k, u64 n, const int* off,
-                           const int* idx, const int* deg, int cap, cudaStream_t st) {
+                           const int* idx, const int* deg, const Arc* arc, int cap,
+                           cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const u64 threads = 256;
   k_pair_cn<<<(unsigned)((n * 32 + threads - 1) / threads), (unsigned)threads, 0, st>>>(
-      links, cnt_rows, k, n, off, idx, deg, cap);
+      links, cnt_rows, k, n, off, idx, deg, arc, cap);
   return cudaGetLastError();
 }
 

@@ -43,7 +43,8 @@ def test_exports_every_declared_symbol(lp):
 
 def test_version_and_options(lp):
     assert "sm_103a" in lp.lp_version()
-    assert lp.lp_get_option(lp.LP_OPT_WARP_MAX_WEDGES) == 512
+    assert lp.lp_get_option(lp.LP_OPT_WARP_MAX_WEDGES) == 256
+    assert lp.lp_get_option(lp.LP_OPT_MED_MAX_WEDGES) == 1024
     lp.lp_set_option(lp.LP_OPT_SPLIT_TARGET, 4096)
     assert lp.lp_get_option(lp.LP_OPT_SPLIT_TARGET) == 4096
     lp.lp_set_option(lp.LP_OPT_SPLIT_TARGET, 6144)

@@ -174,19 +174,20 @@ def test_split_and_dense_items(lp):
     """Tiny tier limits and split tables force CTA items, hash overflows that
     are re-split, and dense-counter items."""
     g = L.chung_lu(3000, 12.0, 2.05, dmax=1500, seed=12)
-    keys = (lp.LP_OPT_WARP_MAX_WEDGES, lp.LP_OPT_CTA_MAX_WEDGES, lp.LP_OPT_SPLIT_TARGET,
-            lp.LP_OPT_SPLIT_LOGCAP)
+    keys = (lp.LP_OPT_WARP_MAX_WEDGES, lp.LP_OPT_MED_MAX_WEDGES, lp.LP_OPT_CTA_MAX_WEDGES,
+            lp.LP_OPT_SPLIT_TARGET, lp.LP_OPT_SPLIT_LOGCAP)
     old = [lp.lp_get_option(x) for x in keys]
     try:
-        for vals in ((8, 513, 256, 6), (64, 1024, 2048, 9), (512, 8192, 6144, 14)):
+        for vals in ((8, 16, 257, 256, 6), (64, 512, 1024, 2048, 9), (256, 1024, 8192, 6144, 14)):
             for x, v in zip(keys, vals):
                 lp.lp_set_option(x, v)
             for m in ("CN", "JC", "RA", "AA"):
                 for cap in (None, 40):
                     got = check_global(lp, g, m, cap, 500)
                     st = lp.lp_last_stats()
-                    if vals[3] == 6 and cap is None:
+                    if vals[4] == 6 and cap is None:
                         assert st["splits"] > 0 and st["cta_items"] > 0
+                        assert all(x > 0 for x in st["tier_launches"])
                 src = np.arange(0, g.n, 7, dtype=np.int32)
                 with lp.Graph.from_csr(g) as G:
                     gl, gc = G.predict_sources(m, src, 10, None)
