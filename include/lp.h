@@ -196,6 +196,32 @@ lp_status lp_set_option(lp_option option, int64_t value);
 /* Current value of a tuning option (-1 if unknown). */
 int64_t lp_get_option(lp_option option);
 
+/*
+ * As lp_predict_sources_dev, but allocates nothing: no cudaMalloc or
+ * cudaFree, no allocating library routine, no host heap use.  This is for
+ * callers that cannot allocate at call time, for example code running under
+ * a memory pool it does not own or on a request path where an allocation
+ * (and the device synchronisation it can cause) is not allowed.  The paper
+ * has no counterpart; it is an integration feature of this library.
+ *   Inputs and outputs are device pointers supplied by the caller, as in
+ *   lp_predict_sources_dev.  All working memory comes from one fixed 32 MiB
+ *   array in device global memory that the library declares statically; each
+ *   device that loads the library holds it until the process exits.
+ *   Limits: n_src <= 2^20 and n_src * (40 + 24 k) bytes plus the work items
+ *   of the sources must fit in the 32 MiB; larger requests are rejected with
+ *   LP_EINVAL and a message (split them into several calls).
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.  Calls are serialised on the host, but every
+ *   call shares the one array: work that overlaps on the GPU from other
+ *   threads or processes using the same library copy must not run at the
+ *   same time (it would race on the array).  Per-call state is cleared at
+ *   the start of each call.
+ */
+lp_status lp_predict_sources_static(const lp_graph* g, lp_measure measure, int32_t degree_cap,
+                                    const int32_t* d_sources, int32_t n_src, int32_t k,
+                                    double threshold, lp_link* d_out, int32_t* d_counts);
+
 /* Statistics of this thread's last predict call. */
 lp_status lp_last_stats(lp_stats* out);
 

@@ -80,6 +80,8 @@ def _load():
                                        ctypes.c_int32, ctypes.c_double, _vp, _vp]
     lib.lp_predict_sources_dev.restype = st
     lib.lp_predict_sources_dev.argtypes = lib.lp_predict_sources.argtypes
+    lib.lp_predict_sources_static.restype = st
+    lib.lp_predict_sources_static.argtypes = lib.lp_predict_sources.argtypes
     lib.lp_last_stats.restype = st
     lib.lp_last_stats.argtypes = [ctypes.POINTER(lp_stats)]
     lib.lp_set_timing.restype = None
@@ -215,6 +217,14 @@ def lp_predict_sources_dev(h, measure, d_sources, n_src: int, k: int, degree_cap
     _check(_load().lp_predict_sources_dev(h, _measure(measure), _cap(degree_cap),
                                           _ptr(d_sources), n_src, k, threshold, _ptr(d_out),
                                           _ptr(d_counts)))
+
+
+def lp_predict_sources_static(h, measure, d_sources, n_src: int, k: int, degree_cap, threshold,
+                              d_out, d_counts) -> None:
+    """Per-source mode without allocation (device pointers; see include/lp.h)."""
+    _check(_load().lp_predict_sources_static(h, _measure(measure), _cap(degree_cap),
+                                             _ptr(d_sources), n_src, k, threshold, _ptr(d_out),
+                                             _ptr(d_counts)))
 
 
 LP_OPT_SELECT_BUFFER, LP_OPT_WARP_MAX_WEDGES, LP_OPT_CTA_MAX_WEDGES, LP_OPT_SPLIT_TARGET, \

@@ -901,6 +901,25 @@ static lp_status check_sources_args(const lp_graph* g, int measure, const void* 
   return LP_OK;
 }
 
+// Entry points for other translation units of the library (thin wrappers).
+lp_status report_error(lp_status s, const char* msg) { return fail(s, "%s", msg); }
+lp_status report_cuda(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+void stats_begin() { begin_stats(); }
+void stats_estimate(const Counters& h) { estimate_stats(h); }
+void stats_add(int64_t candidates, int32_t splits, int32_t launches) {
+  t_stats.candidates += candidates;
+  t_stats.splits += splits;
+  t_stats.launches += launches;
+}
+ScanArgs scan_args(Graph& g, int measure, int cap, double threshold, int mode, int k) {
+  return base_args(g, measure, cap, threshold, mode, k);
+}
+lp_status sources_args_ok(const lp_graph* g, int measure, const void* sources, int n_src, int k,
+                          const void* out, const void* counts) {
+  return check_sources_args(g, measure, sources, n_src, k, out, counts);
+}
+Graph& graph_of(const lp_graph* g) { return *const_cast<lp_graph*>(g); }
+
 }  // namespace lp
 
 extern "C" {

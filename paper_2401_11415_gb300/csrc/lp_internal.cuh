@@ -219,4 +219,14 @@ cudaError_t launch_thresh_worst(const Cand* a, u64 n, Cand* tmp, Thresh* t, cuda
 cudaError_t launch_filter_failed(Cand* d_buf, u64 n, const unsigned char* d_flag,
                                  const int4* d_failed_sorted, int nfailed, Cand* d_out,
                                  Counters* d_ctr, u64* d_count, cudaStream_t st);
+// Helpers of lp_api.cu used by other translation units.
+lp_status report_error(lp_status s, const char* msg);
+lp_status report_cuda(cudaError_t e, const char* what);
+void stats_begin();
+void stats_estimate(const Counters& h);
+void stats_add(int64_t candidates, int32_t splits, int32_t launches);
+ScanArgs scan_args(Graph& g, int measure, int cap, double threshold, int mode, int k);
+lp_status sources_args_ok(const lp_graph* g, int measure, const void* sources, int n_src, int k,
+                          const void* out, const void* counts);
+Graph& graph_of(const lp_graph* g);
 }  // namespace lp
