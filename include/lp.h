@@ -161,7 +161,8 @@ lp_status lp_predict_dev(const lp_graph* g, lp_measure measure, int32_t degree_c
  * Per-source mode: for each sources[i], its k best partners c != sources[i]
  * that are not adjacent to it and score strictly above `threshold`, sorted by
  * (score desc, c asc).  out holds n_src * k links (row i for sources[i]);
- * counts[i] receives the number written to row i (<= k).  1 <= k <=
+ * counts[i] receives the number of links in row i (<= k); the rest of the
+ * row is filled with {u = -1, v = -1, score = 0, cn = 0}.  1 <= k <=
  * LP_MAX_TOPK_PER_SOURCE.  Sources may repeat.  Host pointers.
  */
 lp_status lp_predict_sources(const lp_graph* g, lp_measure measure, int32_t degree_cap,
@@ -221,6 +222,70 @@ int64_t lp_get_option(lp_option option);
 lp_status lp_predict_sources_static(const lp_graph* g, lp_measure measure, int32_t degree_cap,
                                     const int32_t* d_sources, int32_t n_src, int32_t k,
                                     double threshold, lp_link* d_out, int32_t* d_counts);
+
+/* ------------------------------------------------------------ serving --
+ * Continuous batching of per-source top-k queries (lp_predict_sources
+ * semantics, threshold 0) on one resident graph.  Requests of uneven sizes
+ * arrive at any time from any thread; `slots` worker threads each take the
+ * oldest pending request together with every other pending request of the
+ * same (measure, degree_cap, k), up to max_batch_sources sources, and run
+ * them as one device batch on their own CUDA stream, so batches of different
+ * slots overlap on the GPU and requests that arrive while others run join the
+ * next batch.  Each request's result is exactly what lp_predict_sources
+ * returns for it alone.  Not in the paper (a per-vertex serving form of the
+ * ranked top-k list of Section 3).
+ */
+typedef struct {
+  int32_t slots;             /* concurrent device batches, 1..8 (0: 2)           */
+  int32_t max_batch_sources; /* sources per batch and per request (0: 65536)    */
+  int32_t max_pending;       /* queued requests before LP_EBUSY (0: 65536)      */
+  int32_t max_k;             /* largest k accepted, <= LP_MAX_TOPK_PER_SOURCE (0: 16) */
+  int32_t paused;            /* 1: queue requests but start no batch until
+                                lp_serve_resume                                   */
+  int32_t reserved[3];
+} lp_serve_opts;
+
+typedef struct {
+  int64_t submitted;         /* requests accepted                                 */
+  int64_t completed;         /* requests finished (result ready or failed)        */
+  int64_t batches;           /* device batches run                                */
+  int64_t batched_sources;   /* sources over all batches                          */
+  int64_t max_batch_requests;/* most requests merged into one batch               */
+} lp_serve_stats;
+
+/* Start a server on graph g (which must outlive it).  opts may be NULL.
+ * Device memory for the batches is allocated here, not per request. */
+lp_status lp_serve_open(const lp_graph* g, const lp_serve_opts* opts, lp_server** out);
+
+/* Queue a request: host array sources[n_src] (copied; ids checked against
+ * the graph), 1 <= n_src <= max_batch_sources, 1 <= k <= max_k.  Returns at
+ * once with *req_id.  LP_EBUSY if max_pending requests are queued,
+ * LP_EINVAL on bad arguments or after lp_serve_close started. */
+lp_status lp_serve_submit(lp_server* s, const int32_t* sources, int32_t n_src, lp_measure measure,
+                          int32_t degree_cap, int32_t k, uint64_t* req_id);
+
+/* Wait at most timeout_us microseconds (< 0: no limit) for request req_id.
+ * When it is done its result is copied to host out[n_src * k] (row i for
+ * sources[i]) and counts[n_src], the request is released, and its status is
+ * returned.  LP_ETIMEOUT if it is not done in time (the request stays and can
+ * be waited for again); LP_EINVAL for an unknown or already released id. */
+lp_status lp_serve_wait(lp_server* s, uint64_t req_id, int64_t timeout_us, lp_link* out,
+                        int32_t* counts);
+
+/* Let the workers start batches (after lp_serve_open with paused = 1). */
+lp_status lp_serve_resume(lp_server* s);
+
+/* *done = 1 if request req_id has finished, else 0 (LP_EINVAL: unknown id). */
+lp_status lp_serve_poll(lp_server* s, uint64_t req_id, int32_t* done);
+
+/* Counters of the server since lp_serve_open. */
+lp_status lp_serve_get_stats(lp_server* s, lp_serve_stats* out);
+
+/* Finish every queued request (a paused server is resumed), stop the
+ * workers and free the server.  Results not collected with lp_serve_wait are
+ * discarded.  No other call on the server may run concurrently with it or
+ * after it.  NULL accepted. */
+lp_status lp_serve_close(lp_server* s);
 
 /* Statistics of this thread's last predict call. */
 lp_status lp_last_stats(lp_stats* out);

@@ -49,6 +49,18 @@ class lp_stats(ctypes.Structure):
                 ("phase_cycles", ctypes.c_int64 * 6)]
 
 
+class lp_serve_opts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("max_batch_sources", ctypes.c_int32),
+                ("max_pending", ctypes.c_int32), ("max_k", ctypes.c_int32),
+                ("paused", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class lp_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("batched_sources", ctypes.c_int64),
+                ("max_batch_requests", ctypes.c_int64)]
+
+
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _vp = ctypes.c_void_p
 _lib = None
@@ -82,6 +94,21 @@ def _load():
     lib.lp_predict_sources_dev.argtypes = lib.lp_predict_sources.argtypes
     lib.lp_predict_sources_static.restype = st
     lib.lp_predict_sources_static.argtypes = lib.lp_predict_sources.argtypes
+    lib.lp_serve_open.restype = st
+    lib.lp_serve_open.argtypes = [_vp, ctypes.POINTER(lp_serve_opts), ctypes.POINTER(_vp)]
+    lib.lp_serve_submit.restype = st
+    lib.lp_serve_submit.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.c_int, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]
+    lib.lp_serve_wait.restype = st
+    lib.lp_serve_wait.argtypes = [_vp, ctypes.c_uint64, ctypes.c_int64, _vp, _vp]
+    lib.lp_serve_poll.restype = st
+    lib.lp_serve_poll.argtypes = [_vp, ctypes.c_uint64, _i32p]
+    lib.lp_serve_resume.restype = st
+    lib.lp_serve_resume.argtypes = [_vp]
+    lib.lp_serve_get_stats.restype = st
+    lib.lp_serve_get_stats.argtypes = [_vp, ctypes.POINTER(lp_serve_stats)]
+    lib.lp_serve_close.restype = st
+    lib.lp_serve_close.argtypes = [_vp]
     lib.lp_last_stats.restype = st
     lib.lp_last_stats.argtypes = [ctypes.POINTER(lp_stats)]
     lib.lp_set_timing.restype = None
@@ -290,3 +317,62 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------- serving --
+
+class Server:
+    """lp_serve_* wrapper: continuous batching of per-source queries."""
+
+    def __init__(self, graph, slots=0, max_batch_sources=0, max_pending=0, max_k=0,
+                 paused=False):
+        o = lp_serve_opts(slots, max_batch_sources, max_pending, max_k, 1 if paused else 0)
+        h = _vp()
+        _check(_load().lp_serve_open(graph.handle if isinstance(graph, Graph) else graph,
+                                     ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h
+        self._sizes = {}
+
+    def submit(self, sources, measure, k, degree_cap=None) -> int:
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        rid = ctypes.c_uint64()
+        _check(_load().lp_serve_submit(self.handle, src.ctypes.data, src.size, _measure(measure),
+                                       _cap(degree_cap), k, ctypes.byref(rid)))
+        self._sizes[rid.value] = (src.size, k)
+        return rid.value
+
+    def wait(self, req_id: int, timeout_us: int = -1):
+        n, k = self._sizes.get(req_id, (0, 1))
+        out = np.zeros(max(n * k, 1), dtype=LINK_DTYPE)
+        counts = np.zeros(max(n, 1), dtype=np.int32)
+        st = _load().lp_serve_wait(self.handle, req_id, timeout_us, out.ctypes.data,
+                                   counts.ctypes.data)
+        if st != LP_ETIMEOUT:
+            self._sizes.pop(req_id, None)
+        _check(st)
+        return out[: n * k].reshape(n, k), counts[:n].copy()
+
+    def poll(self, req_id: int) -> bool:
+        d = ctypes.c_int32()
+        _check(_load().lp_serve_poll(self.handle, req_id, ctypes.byref(d)))
+        return bool(d.value)
+
+    def resume(self):
+        _check(_load().lp_serve_resume(self.handle))
+
+    def stats(self) -> dict:
+        s = lp_serve_stats()
+        _check(_load().lp_serve_get_stats(self.handle, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in lp_serve_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            _load().lp_serve_close(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+

@@ -133,10 +133,12 @@ static void free_graph(Graph* g) {
                            &g->s_cnt, &g->s_links, &g->s_src, &g->s_grp};
   for (auto* s : all)
     if (s->p) cudaFree(s->p);
-  cudaFree(g->d_off);
-  cudaFree(g->d_idx);
-  cudaFree(g->d_deg);
-  cudaFree(g->d_arc);
+  if (g->owns_arrays) {
+    cudaFree(g->d_off);
+    cudaFree(g->d_idx);
+    cudaFree(g->d_deg);
+    cudaFree(g->d_arc);
+  }
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : g->kev)
@@ -773,7 +775,8 @@ static lp_status predict_sources(Graph& g, int measure, int cap, const int* d_sr
     if (bad) return fail(LP_EINVAL, "lp_predict_sources: source id out of range");
   }
   CU(cudaMemsetAsync(d_counts, 0, sizeof(int) * (size_t)n_src, st));
-  if (cap == 0 || g.n == 0) {
+  if (cap == 0 || g.n == 0) {  // nothing to predict: rows of fillers
+    CU(launch_emit_sources(nullptr, d_counts, d_src, n_src, k, measure, g.fixbits, d_out, st));
     CU(cudaStreamSynchronize(st));
     return LP_OK;
   }
@@ -919,6 +922,41 @@ lp_status sources_args_ok(const lp_graph* g, int measure, const void* sources, i
   return check_sources_args(g, measure, sources, n_src, k, out, counts);
 }
 Graph& graph_of(const lp_graph* g) { return *const_cast<lp_graph*>(g); }
+
+lp_status make_shadow(const Graph& g, Graph** out) {
+  lp_graph* s = new (std::nothrow) lp_graph();
+  if (!s) return fail(LP_ENOMEM, "shadow graph: host allocation");
+  s->owns_arrays = false;
+  s->device = g.device;
+  s->n = g.n;
+  s->arcs = g.arcs;
+  s->dmax = g.dmax;
+  s->fixbits = g.fixbits;
+  s->d_off = g.d_off;
+  s->d_idx = g.d_idx;
+  s->d_deg = g.d_deg;
+  s->d_arc = g.d_arc;
+  cudaError_t e = cudaSetDevice(g.device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->ev[i]);
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->kev[i]);
+  if (e != cudaSuccess) {
+    free_graph(s);
+    return cuda_fail(e, "shadow graph");
+  }
+  *out = s;
+  return LP_OK;
+}
+
+void destroy_shadow(Graph* s) { free_graph(s); }
+
+lp_status run_sources_dev(Graph& g, int measure, int cap, const int* d_src, int n_src, int k,
+                          double threshold, lp_link* d_out, int* d_counts) {
+  std::lock_guard<std::mutex> lock(g.mu);
+  cudaError_t e = cudaSetDevice(g.device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  return predict_sources(g, measure, cap, d_src, n_src, k, threshold, d_out, d_counts);
+}
 
 }  // namespace lp
 

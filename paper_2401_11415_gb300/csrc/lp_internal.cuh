@@ -145,6 +145,7 @@ Options options_snapshot();
 
 // Host-side graph object.
 struct Graph {
+  bool owns_arrays = true;  // false for a shadow that shares another graph's arrays
   int device = 0;
   int32_t n = 0;
   int64_t arcs = 0;
@@ -229,4 +230,10 @@ ScanArgs scan_args(Graph& g, int measure, int cap, double threshold, int mode, i
 lp_status sources_args_ok(const lp_graph* g, int measure, const void* sources, int n_src, int k,
                           const void* out, const void* counts);
 Graph& graph_of(const lp_graph* g);
+// A graph view sharing g's device arrays with its own stream, events and
+// scratch (for concurrent workers); freed with destroy_shadow.
+lp_status make_shadow(const Graph& g, Graph** out);
+void destroy_shadow(Graph* s);
+lp_status run_sources_dev(Graph& g, int measure, int cap, const int* d_src, int n_src, int k,
+                          double threshold, lp_link* d_out, int* d_counts);
 }  // namespace lp

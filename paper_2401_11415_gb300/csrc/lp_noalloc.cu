@@ -119,8 +119,9 @@ static lp_status run_static(Graph& g, int measure, int cap, const int* d_src, in
   if (bad) return report_error(LP_EINVAL, "lp_predict_sources_static: source id out of range");
   e = cudaMemsetAsync(d_counts, 0, sizeof(int) * (size_t)n_src, st);
   if (e != cudaSuccess) return report_cuda(e, "lp_predict_sources_static: clear counts");
-  if (cap == 0 || g.n == 0) {
-    e = cudaStreamSynchronize(st);
+  if (cap == 0 || g.n == 0) {  // nothing to predict: rows of fillers
+    e = launch_emit_sources(nullptr, d_counts, d_src, n_src, k, measure, g.fixbits, d_out, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? LP_OK : report_cuda(e, "lp_predict_sources_static");
   }
 

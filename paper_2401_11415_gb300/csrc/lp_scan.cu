@@ -1464,7 +1464,15 @@ __global__ void k_emit_sources(const TopEnt* __restrict__ top, const int* __rest
   const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (u64)n_src * k) return;
   const int r = (int)(i / k), j = (int)(i % k);
-  if (j >= cnt[r]) return;
+  if (j >= cnt[r]) {  // unused entry of the row: a fixed filler
+    lp_link L;
+    L.u = -1;
+    L.v = -1;
+    L.score = 0.f;
+    L.cn = 0;
+    out[i] = L;
+    return;
+  }
   const TopEnt x = top[i];
   out[i] = make_link(measure, sources[r], x.c, x.num, x.den, (u64)x.cn, fixbits);
 }

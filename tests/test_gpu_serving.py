@@ -1,0 +1,113 @@
+"""lp_serve_*: continuous batching of per-source queries (needs a GPU).
+
+Each served result must equal lp_predict_sources on the same sources alone,
+whatever else is in the batch; requests of uneven sizes and different
+(measure, hub limit, k) arrive from several threads.  Bounded waits, a full
+queue and bad requests are made on the host side (a paused server), never by
+stalling the GPU.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+import lp_inputs as L
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_11415_gb300 import _build
+    _build.build()
+    import paper_2401_11415_gb300 as m
+    torch.cuda.init()
+    return m
+
+
+@pytest.fixture(scope="module")
+def graph():
+    return L.chung_lu(6000, 12.0, 2.1, dmax=1200, seed=31)
+
+
+KINDS = [("JC", 64, 10), ("RA", None, 5), ("CN", 16, 8), ("AA", 256, 10)]
+
+
+def test_served_equals_alone(lp, graph):
+    g = graph
+    rng = np.random.default_rng(7)
+    reqs = []
+    for i in range(160):
+        n = int(np.exp(rng.uniform(0, np.log(400))))
+        reqs.append((rng.integers(0, g.n, n).astype(np.int32), KINDS[i % len(KINDS)]))
+    with lp.Graph.from_csr(g) as G:
+        expect = [G.predict_sources(kind[0], src, kind[2], kind[1]) for src, kind in reqs]
+        with lp.Server(G, slots=3, max_batch_sources=2000, max_k=16) as S:
+            ids = [None] * len(reqs)
+
+            def submit(lo, hi):
+                for i in range(lo, hi):
+                    src, (m, cap, k) = reqs[i]
+                    ids[i] = S.submit(src, m, k, cap)
+
+            th = [threading.Thread(target=submit, args=(j * 40, (j + 1) * 40)) for j in range(4)]
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+            got = [S.wait(ids[i], 60_000_000) for i in range(len(reqs))]
+            st = S.stats()
+        assert st["submitted"] == st["completed"] == len(reqs)
+        assert st["max_batch_requests"] > 1        # requests were merged into batches
+        for (gl, gc), (el, ec) in zip(got, expect):
+            assert np.array_equal(gc, ec)
+            assert gl.tobytes() == el.tobytes()
+
+
+def test_paused_timeout_full_queue_and_errors(lp, graph):
+    g = graph
+    src = np.arange(50, dtype=np.int32)
+    with lp.Graph.from_csr(g) as G:
+        with lp.Server(G, slots=1, max_pending=3, max_batch_sources=100, paused=True) as S:
+            a = S.submit(src, "JC", 10, 64)
+            b = S.submit(src[:7], "JC", 10, 64)
+            c = S.submit(src[:3], "RA", 5, None)
+            with pytest.raises(lp.LPError) as e:
+                S.submit(src, "JC", 10, 64)                 # fourth queued request
+            assert e.value.status == lp.LP_EBUSY
+            with pytest.raises(lp.LPError) as e:
+                S.wait(a, 2000)                              # paused: cannot finish
+            assert e.value.status == lp.LP_ETIMEOUT
+            assert not S.poll(a)
+            for bad in (dict(sources=np.array([g.n], np.int32), measure="JC", k=5),
+                        dict(sources=src, measure="JC", k=17),
+                        dict(sources=np.arange(101, dtype=np.int32), measure="JC", k=5)):
+                with pytest.raises(lp.LPError) as e:
+                    S.submit(bad["sources"], bad["measure"], bad["k"])
+                assert e.value.status == lp.LP_EINVAL
+            S.resume()
+            ra = S.wait(a, 60_000_000)
+            rb = S.wait(b, 60_000_000)
+            rc = S.wait(c, 60_000_000)
+            with pytest.raises(lp.LPError) as e:
+                S.wait(a, 1000)                              # already released
+            assert e.value.status == lp.LP_EINVAL
+            assert S.stats()["max_batch_requests"] >= 2      # a and b shared a batch
+        ea = G.predict_sources("JC", src, 10, 64)
+        assert ra[0].tobytes() == ea[0].tobytes()
+        eb = G.predict_sources("JC", src[:7], 10, 64)
+        assert rb[0].tobytes() == eb[0].tobytes()
+        ec = G.predict_sources("RA", src[:3], 5, None)
+        assert rc[0].tobytes() == ec[0].tobytes()
+
+
+def test_close_finishes_queued_requests(lp, graph):
+    g = graph
+    with lp.Graph.from_csr(g) as G:
+        S = lp.Server(G, slots=2, paused=True)
+        for i in range(10):
+            S.submit(np.arange(i * 10, i * 10 + 10, dtype=np.int32), "CN", 4)
+        S.close()                                            # resumes, drains, frees
