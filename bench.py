@@ -310,6 +310,109 @@ def cpu_baseline(split):
                       "bound the run"}
 
 
+# ------------------------------------------------------------ serving ----
+
+def run_serve(args):
+    """Per-source serving on R-MAT scale 24 (requests of 1-4096 sources, top-10
+    DLH(256) RA, Poisson arrivals): one plain lp_predict_sources call per
+    request in FIFO order versus lp_serve_* continuous batching."""
+    import threading
+    import torch
+    import lp_inputs as L
+    import paper_2401_11415_gb300 as lp
+    from paper_2401_11415_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    scale = args.scale if args.scale != 20 else 24
+    t0 = time.perf_counter()
+    g = L.rmat(scale, 16, seed=1)
+    t_gen = time.perf_counter() - t0
+    rng = np.random.default_rng(11)
+    live_v = np.nonzero(np.diff(g.off) > 0)[0].astype(np.int32)
+    R = args.requests
+    sizes = np.exp(rng.uniform(0, np.log(4096), R)).astype(np.int64).clip(1, 4096)
+    reqs = [live_v[rng.integers(0, live_v.size, int(m))] for m in sizes]
+    measure, cap, k = "RA", 256, 10
+    t0 = time.perf_counter()
+    G = lp.Graph.from_csr(g)
+    t_create = time.perf_counter() - t0
+    for r in reqs[:5]:
+        G.predict_sources(measure, r, k, cap)
+    # plain service times, serialised
+    plain_res, svc = [], []
+    for r in reqs:
+        t = time.perf_counter()
+        plain_res.append(G.predict_sources(measure, r, k, cap))
+        svc.append(time.perf_counter() - t)
+    svc = np.array(svc)
+    mu = R / svc.sum()
+    edges = int(sum(int(c.sum()) for _, c in plain_res))
+    out = {"metric": "served per-source top-10 DLH(256) RA: p50/p99 latency and edges/s",
+           "workload": f"R-MAT scale {scale} (n={g.n}, {g.edges} undirected edges), {R} requests "
+                       "of 1-4096 sources (log-uniform), Poisson arrivals",
+           "graph_generate_s": round(t_gen, 1), "graph_create_s": round(t_create, 2),
+           "plain_capacity_req_per_s": round(mu, 1), "predicted_edges": edges, "loads": []}
+    for rho in args.loads:
+        lam = rho * mu
+        arr = np.cumsum(rng.exponential(1.0 / lam, R))
+        # plain: FIFO, one call per request, real time
+        t_start = time.perf_counter()
+        lat_p = np.zeros(R)
+        for i, r in enumerate(reqs):
+            now = time.perf_counter() - t_start
+            if now < arr[i]:
+                time.sleep(arr[i] - now)
+            G.predict_sources(measure, r, k, cap)
+            lat_p[i] = (time.perf_counter() - t_start) - arr[i]
+        span_p = time.perf_counter() - t_start
+        # served: submit at arrival times, several waiters
+        S = lp.Server(G, slots=args.slots, max_batch_sources=65536, max_k=16)
+        ids = [None] * R
+        lat_s = np.zeros(R)
+        got = [None] * R
+        ready = [threading.Event() for _ in range(R)]
+        t_start = time.perf_counter()
+
+        def submitter():
+            for i, r in enumerate(reqs):
+                now = time.perf_counter() - t_start
+                if now < arr[i]:
+                    time.sleep(arr[i] - now)
+                ids[i] = S.submit(r, measure, k, cap)
+                ready[i].set()
+
+        def waiter(j, nw):
+            for i in range(j, R, nw):
+                ready[i].wait()
+                got[i] = S.wait(ids[i], -1)
+                lat_s[i] = (time.perf_counter() - t_start) - arr[i]
+
+        nw = 8
+        th = [threading.Thread(target=submitter)] + \
+             [threading.Thread(target=waiter, args=(j, nw)) for j in range(nw)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        span_s = time.perf_counter() - t_start
+        st = S.stats()
+        S.close()
+        same = all(got[i][0].tobytes() == plain_res[i][0].tobytes() and
+                   np.array_equal(got[i][1], plain_res[i][1]) for i in range(R))
+        out["loads"].append({
+            "load": rho, "arrival_req_per_s": round(lam, 1),
+            "plain": {"p50_ms": round(1e3 * float(np.percentile(lat_p, 50)), 2),
+                      "p99_ms": round(1e3 * float(np.percentile(lat_p, 99)), 2),
+                      "edges_per_s": round(edges / span_p, 1)},
+            "served": {"p50_ms": round(1e3 * float(np.percentile(lat_s, 50)), 2),
+                       "p99_ms": round(1e3 * float(np.percentile(lat_s, 99)), 2),
+                       "edges_per_s": round(edges / span_s, 1),
+                       "batches": st["batches"], "max_batch_requests": st["max_batch_requests"]},
+            "identical_to_plain": bool(same)})
+    G.close()
+    return out
+
+
 # ------------------------------------------------------- reference arm ----
 
 def run_reference(args, rank, world):
@@ -389,13 +492,21 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only", default="", help="subset of calls, e.g. JC@inf,RA@256")
     ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (20 = the workload)")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "serve"],
+                    help="sweep: the DLH cap sweep (the benchmark line); serve: serving study")
+    ap.add_argument("--requests", type=int, default=1500, help="serve: number of requests")
+    ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.9, 2.0],
+                    help="serve: arrival rates as multiples of the plain capacity")
+    ap.add_argument("--slots", type=int, default=2, help="serve: server slots")
     ap.add_argument("--select-buffer", type=int, default=0,
                     help="minimum selection-buffer capacity (candidates); 0 = library default")
     args = ap.parse_args()
     global _ARGS
     _ARGS = args
     rank, world, local = dist_init()
-    if args.impl == "reference":
+    if args.workload == "serve":
+        line = run_serve(args) if rank == 0 else None
+    elif args.impl == "reference":
         line = run_reference(args, rank, world)
     else:
         line = run_ours(args, rank, world, local)
