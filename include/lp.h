@@ -181,14 +181,18 @@ typedef enum {
                                  (default 8388608; 24 bytes each, twice)       */
   LP_OPT_WARP_MAX_WEDGES = 2, /* warp tier: sources with W <= this (1..256, 256) */
   LP_OPT_CTA_MAX_WEDGES = 3,  /* one large item per source up to W (257..8192, 8192) */
-  LP_OPT_SPLIT_TARGET = 4,    /* wedges per split hash item (256..12288, 6144) */
+  LP_OPT_SPLIT_TARGET = 4,    /* wedges per split hash item (256..12288, 6144),
+                                 halved per log2 step the table is below LOGCAP */
   LP_OPT_SPLIT_LOGCAP = 5,    /* log2 slots of a split hash item (6..14, 14)     */
   LP_OPT_MED_MAX_WEDGES = 6,  /* medium tier: W <= this (1..1024, 1024); the
                                  warp tier takes precedence                     */
   LP_OPT_ITEM_WEDGES = 7,     /* target wedges of one dense sweep item
                                  (1024..2^30, 262144)                           */
-  LP_OPT_PHASE_PROFILE = 8    /* 1: record per-phase clock cycles of the large
+  LP_OPT_PHASE_PROFILE = 8,   /* 1: record per-phase clock cycles of the large
                                  tier in lp_stats.phase_cycles (0..1, 0)        */
+  LP_OPT_BIG_CTA_THREADS = 9  /* threads of a large-tier CTA: 1024 (one per SM,
+                                 192 KB table) or 512 (two per SM, 98 KB each;
+                                 split targets shrink with the table) (1024)   */
 } lp_option;
 
 /* Set a tuning option; LP_EINVAL if the option or value is out of range. */

@@ -255,8 +255,8 @@ def lp_predict_sources_static(h, measure, d_sources, n_src: int, k: int, degree_
 
 
 LP_OPT_SELECT_BUFFER, LP_OPT_WARP_MAX_WEDGES, LP_OPT_CTA_MAX_WEDGES, LP_OPT_SPLIT_TARGET, \
-    LP_OPT_SPLIT_LOGCAP, LP_OPT_MED_MAX_WEDGES, LP_OPT_ITEM_WEDGES, LP_OPT_PHASE_PROFILE = \
-    range(1, 9)
+    LP_OPT_SPLIT_LOGCAP, LP_OPT_MED_MAX_WEDGES, LP_OPT_ITEM_WEDGES, LP_OPT_PHASE_PROFILE, \
+    LP_OPT_BIG_CTA_THREADS = range(1, 10)
 
 
 def lp_set_option(option: int, value: int) -> None:

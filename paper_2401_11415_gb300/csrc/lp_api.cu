@@ -138,6 +138,7 @@ static void free_graph(Graph* g) {
     cudaFree(g->d_idx);
     cudaFree(g->d_deg);
     cudaFree(g->d_arc);
+    cudaFree(g->d_wt);
   }
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
@@ -180,6 +181,10 @@ lp_status lp_set_option(lp_option option, int64_t value) {
       if (value < 0 || value > 1) break;
       lp::g_opt.phase_profile = (int)value;
       return LP_OK;
+    case LP_OPT_BIG_CTA_THREADS:
+      if (value != 512 && value != 1024) break;
+      lp::g_opt.big_threads = (int)value;
+      return LP_OK;
     case LP_OPT_CTA_MAX_WEDGES:
       if (value < 257 || value > lp::kCtaMaxWedges) break;
       lp::g_opt.cta_max = (int)value;
@@ -210,6 +215,7 @@ int64_t lp_get_option(lp_option option) {
     case LP_OPT_MED_MAX_WEDGES: return o.med_max;
     case LP_OPT_ITEM_WEDGES: return o.item_wedges;
     case LP_OPT_PHASE_PROFILE: return o.phase_profile;
+    case LP_OPT_BIG_CTA_THREADS: return o.big_threads;
     default: return -1;
   }
 }
@@ -311,6 +317,7 @@ lp_status lp_graph_create(int32_t n, const int32_t* offsets, const int32_t* indi
   if (e == cudaSuccess) e = cudaMalloc(&g->d_idx, sizeof(int) * (size_t)(A > 0 ? A : 1));
   if (e == cudaSuccess) e = cudaMalloc(&g->d_deg, sizeof(int) * (size_t)(n > 0 ? n : 1));
   if (e == cudaSuccess) e = cudaMalloc(&g->d_arc, sizeof(Arc) * (size_t)(A > 0 ? A : 1));
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_wt, sizeof(u64) * 2 * ((size_t)dmax + 1));
   if (e == cudaSuccess) e = cudaMalloc(&d_err, sizeof(int));
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->ev[i]);
   for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->kev[i]);
@@ -327,6 +334,7 @@ lp_status lp_graph_create(int32_t n, const int32_t* offsets, const int32_t* indi
                                                     d_err);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = launch_build_weights(dmax, g->fixbits, g->d_wt, g->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
@@ -427,11 +435,18 @@ static ScanArgs base_args(Graph& g, int measure, int cap, double threshold, int 
   const Options o = options_snapshot();
   const bool v64 = measure == LP_AA || measure == LP_RA;
   const int vbytes = v64 ? 8 : 4;
+  const int bt = o.big_threads;
+  const int tops = mode == 1 ? (bt / 32) * k * (int)sizeof(TopEnt) : 0;
   int big_bytes = kCtaSmem;
-  if (mode == 1) {
-    const int avail = 227 * 1024 - 2048 - kBigExtraSmem - kCtaWarps * k * (int)sizeof(TopEnt);
-    if (avail < big_bytes) big_bytes = avail & ~1023;
+  if (bt == 1024) {
+    if (mode == 1) {
+      const int avail = 227 * 1024 - 2048 - big_extra_smem(1024) - tops;
+      if (avail < big_bytes) big_bytes = avail & ~1023;
+    }
+  } else {  // two CTAs per SM: half the SM's shared memory each (1 KB for statics)
+    big_bytes = (kSmemPerSm / 2 - kSmemPerCtaReserved - 1024 - big_extra_smem(bt) - tops) & ~1023;
   }
+  A.big_threads = bt;
   int big_logcap = 0;
   while ((2ll << big_logcap) * (4 + vbytes) <= big_bytes) ++big_logcap;
   A.big_bytes = big_bytes;
@@ -441,12 +456,14 @@ static ScanArgs base_args(Graph& g, int measure, int cap, double threshold, int 
   A.warp_max = std::min(o.warp_max, kWarpMaxWedges);
   A.med_max = std::max(A.warp_max, std::min(o.med_max, kMedMaxWedges));
   A.cta_max = std::max(A.med_max, std::min(o.cta_max, 1 << (big_logcap - 1)));
-  A.split_target = o.split_target;
   A.item_wedges = (int)o.item_wedges;
   A.split_logcap = std::min(o.split_logcap, big_logcap);
+  // a smaller split table than asked for takes proportionally fewer wedges
+  A.split_target = std::max(256, o.split_target >> (o.split_logcap - A.split_logcap));
   A.off = g.d_off;
   A.idx = g.d_idx;
   A.deg = g.d_deg;
+  A.wt = measure == LP_AA ? g.d_wt : (measure == LP_RA ? g.d_wt + (size_t)g.dmax + 1 : nullptr);
   A.arc = g.d_arc;
   A.n = g.n;
   A.cap = cap < 0 ? INT32_MAX : cap;
@@ -936,6 +953,7 @@ lp_status make_shadow(const Graph& g, Graph** out) {
   s->d_idx = g.d_idx;
   s->d_deg = g.d_deg;
   s->d_arc = g.d_arc;
+  s->d_wt = g.d_wt;
   cudaError_t e = cudaSetDevice(g.device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->ev[i]);

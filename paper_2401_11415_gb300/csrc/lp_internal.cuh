@@ -27,10 +27,14 @@ constexpr int kCtaWarps = kCtaThreads / 32;
 constexpr int kCtaSlots = 16384;         // largest CTA hash table
 constexpr int kCtaMaxWedges = 8192;      // single-item hash: W <= this
 constexpr int kSplitTarget = 6144;       // wedges per split hash item
-constexpr int kCtaSmem = 192 * 1024;     // table bytes of a large-tier CTA
-// shared memory of a large-tier CTA beyond its table: 2048 arc cursors and a
-// queue of 768 long segments (start, length, piece prefix, weight)
-constexpr int kBigExtraSmem = 2048 * 4 + 768 * (4 + 4 + 4 + 8);
+constexpr int kCtaSmem = 192 * 1024;     // table bytes of a 1024-thread large-tier CTA
+// shared memory of a large-tier CTA of `threads` threads beyond its table:
+// 4 * threads window boundaries (or arc cursors) and one chunk of `threads`
+// arcs (wedge prefix, segment base, weight)
+constexpr int big_extra_smem(int threads) { return threads * 4 * 4 + threads * (4 + 4 + 8); }
+// shared memory the large tier may use per SM (two 512-thread CTAs share it)
+constexpr int kSmemPerSm = 228 * 1024;
+constexpr int kSmemPerCtaReserved = 1024;
 
 // Item kinds (int4.w of a CTA work record).
 constexpr int kItemDense = 1;    // dense counters over [lo, hi)
@@ -92,6 +96,7 @@ struct ScanArgs {
   const int* idx;
   const int* deg;
   const Arc* arc;
+  const u64* wt;      // AA / RA: fixed-point weight by intermediary degree
   int n;
   int cap;            // hub limit; INT32_MAX for none
   int measure;
@@ -127,6 +132,7 @@ struct ScanArgs {
   int big_span;        // dense window of a large-tier item (vertices)
   int big_bytes;       // table bytes of a large-tier CTA
   int item_wedges;     // target wedges of one dense sweep item
+  int big_threads;     // threads of a large-tier CTA: 1024 (one per SM) or 512 (two)
   u64* prof;           // optional: large-tier phase cycles (6 entries) or null
 };
 
@@ -140,6 +146,7 @@ struct Options {
   int split_logcap = 14;
   long long item_wedges = 1 << 18;
   int phase_profile = 0;
+  int big_threads = 1024;
 };
 Options options_snapshot();
 
@@ -156,6 +163,7 @@ struct Graph {
   int* d_idx = nullptr;
   int* d_deg = nullptr;
   Arc* d_arc = nullptr;
+  u64* d_wt = nullptr;     // [2 * (dmax + 1)]: AA then RA weight by degree
   std::mutex mu;
   // scratch, grown on demand
   struct Scratch {
@@ -199,6 +207,7 @@ cudaError_t launch_set_thresh(const Cand* sorted, u64 k, Thresh* t, cudaStream_t
 cudaError_t launch_scan_warp(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
 cudaError_t launch_scan_cta(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
 cudaError_t launch_scan_med(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
+cudaError_t launch_build_weights(int dmax, int fixbits, u64* wt, cudaStream_t st);
 cudaError_t launch_estimate2(const ScanArgs& A, int n_rec, int4* warpq, int4* medq, int4* itemq,
                              u64 itemq_cap, int2* grp, cudaStream_t st);
 cudaError_t launch_merge_partials(const int4* grp_list, int ngrp, const int* order,

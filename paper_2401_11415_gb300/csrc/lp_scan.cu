@@ -33,6 +33,7 @@
 #include <float.h>
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "lp_internal.cuh"
@@ -51,14 +52,35 @@ __host__ __device__ __forceinline__ int ceil_log2(u64 x) {
   return l;
 }
 
-// Fixed-point weight that intermediary b of degree db adds (Algorithm 1,
-// scanEdges: 1/log|Gamma_b| for AA, 1/|Gamma_b| for RA, 1 otherwise).
-template <typename V>
-__device__ __forceinline__ V arc_weight(int measure, int db, int fixbits) {
-  if (sizeof(V) == 8) {
-    if (measure == LP_RA) return (V)__double2ull_rn(ldexp(1.0, fixbits) / (double)db);
-    return (V)__double2ull_rn(ldexp(1.0, fixbits) / log((double)db));
+// Fixed-point weight that an intermediary of degree db adds (Algorithm 1,
+// scanEdges: 1/log|Gamma_b| for AA, 1/|Gamma_b| for RA), rounded to
+// nearest at fixbits fraction bits.  Intermediaries have degree >= 2.
+__device__ __forceinline__ u64 fixed_weight(int measure, int db, int fixbits) {
+  if (db < 2) return 0;
+  if (measure == LP_RA) return __double2ull_rn(ldexp(1.0, fixbits) / (double)db);
+  return __double2ull_rn(ldexp(1.0, fixbits) / log((double)db));
+}
+
+// The graph's weight tables, by degree: wt[d] (AA) and wt[dmax + 1 + d] (RA).
+__global__ void k_build_weights(int dmax, int fixbits, u64* __restrict__ wt) {
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d <= dmax; d += gridDim.x * blockDim.x) {
+    wt[d] = fixed_weight(LP_AA, d, fixbits);
+    wt[(size_t)dmax + 1 + d] = fixed_weight(LP_RA, d, fixbits);
   }
+}
+
+cudaError_t launch_build_weights(int dmax, int fixbits, u64* wt, cudaStream_t st) {
+  const int threads = 256;
+  const int blocks = (int)std::min<long long>(((long long)dmax + threads) / threads, 4096);
+  k_build_weights<<<blocks, threads, 0, st>>>(dmax, fixbits, wt);
+  return cudaGetLastError();
+}
+
+// Weight that intermediary b of degree db adds to each of its wedges: 1 for
+// the count measures, the table entry for AA and RA (no FP64 in the scan).
+template <typename V>
+__device__ __forceinline__ V arc_weight(const ScanArgs& A, int db) {
+  if (sizeof(V) == 8) return (V)__ldg(A.wt + db);
   return (V)1;
 }
 
@@ -356,6 +378,25 @@ __device__ __forceinline__ void scan_arcs(int s, int len, V w, const int* __rest
 
 // ----------------------------------------------------------- hash tables --
 
+// Shared-memory accumulate.  A 64-bit value is added as two 32-bit atomics:
+// the low word, then the high word plus the carry out of the low word (the
+// 32-bit shared atomics run several times faster than the 64-bit one).  The
+// value is exact once all adds are done, since each wrap of the low word is
+// paid by the add that caused it; nothing reads it before then.  Returns the
+// old low word (0 on the first add to a zero counter).
+template <typename V>
+__device__ __forceinline__ u32 shared_add(V* p, V w) {
+  if (sizeof(V) == 8) {
+    u32* q = reinterpret_cast<u32*>(p);
+    const u32 l = (u32)w, h = (u32)((u64)w >> 32);
+    const u32 old = atomicAdd(q, l);
+    const u32 hc = h + ((old + l < old) ? 1u : 0u);
+    if (hc) atomicAdd(q + 1, hc);
+    return old;
+  }
+  return atomicAdd(reinterpret_cast<u32*>(p), (u32)w);
+}
+
 // Add w to key c (stored as c + 1).  Returns 1 if c was new, 0 if it
 // existed, 2 if the table had no free slot (bounded probe count).
 template <typename V>
@@ -366,13 +407,13 @@ __device__ __forceinline__ int hash_add(int* keys, V* vals, int logcap, int c, V
   for (u32 probe = 0; probe <= mask; ++probe) {
     const int k = ((volatile int*)keys)[h];
     if (k == key) {
-      atomicAdd(&vals[h], w);
+      shared_add<V>(&vals[h], w);
       return 0;
     }
     if (k == kEmpty) {
       const int old = atomicCAS(&keys[h], kEmpty, key);
       if (old == kEmpty || old == key) {
-        atomicAdd(&vals[h], w);
+        shared_add<V>(&vals[h], w);
         return old == kEmpty ? 1 : 0;
       }
     }
@@ -489,6 +530,41 @@ __device__ __forceinline__ int nth_set_bit(u32 mask, int n) {
   return pos;
 }
 
+// The measures that read |Gamma_c| do not increase with it, and |Gamma_c| is
+// at least the count v (each counted intermediary is a neighbour of c), so
+// the key taken with |Gamma_c| = v bounds the true key from above.  True when
+// that bound already ranks strictly below tn/td: the pair cannot pass and
+// |Gamma_c| need not be read.
+__device__ __forceinline__ bool bound_below(int measure, u64 v, u64 da, u64 tn, u64 td) {
+  u64 un, ud;
+  make_key(measure, v, da, v, un, ud);
+  const u64 lh = __umul64hi(un, td), ll = un * td;
+  const u64 rh = __umul64hi(tn, ud), rl = tn * ud;
+  return lh < rh || (lh == rh && ll < rl);
+}
+
+// Key of candidate c (count or fixed-point sum v) and whether it can enter the
+// selection: S_th (strict), then in the global mode the admission threshold
+// T, in the per-source mode the warp's full top-k list (bound test only; the
+// exact test is top_offer's).
+template <typename V, int MODE>
+__device__ __forceinline__ bool key_passes(const ScanArgs& A, const Thresh& T, int a, u64 da,
+                                           int c, V v, const TopEnt* top, int tcnt, u64& num,
+                                           u64& den) {
+  u64 dc = 0;
+  if (needs_dc(A.measure)) {
+    if (MODE == 0 && T.valid && bound_below(A.measure, (u64)v, da, T.num, T.den)) return false;
+    if (MODE == 1 && tcnt >= A.k &&
+        bound_below(A.measure, (u64)v, da, top[A.k - 1].num, top[A.k - 1].den))
+      return false;
+    dc = (u64)__ldg(A.deg + c);
+  }
+  make_key(A.measure, (u64)v, da, dc, num, den);
+  bool pass = !A.thr_check || key_value(A.measure, num, den, (u64)v, A.fixbits) > A.threshold;
+  if (MODE == 0 && pass && T.valid) pass = before(num, den, a, c, T.num, T.den, T.u, T.v);
+  return pass;
+}
+
 // Score the live entries among four table slots per lane (value 0 = empty or
 // dead): the live ones are first gathered across the warp, then scored 32 at
 // a time with every lane busy.  Returns true if the global buffer
@@ -507,7 +583,6 @@ __device__ __forceinline__ bool score_chunk(const ScanArgs& A, const Thresh& T, 
     pre[j + 1] = pre[j] + __popc(m[j]);
   }
   const int L = pre[4];
-  const bool dc_needed = needs_dc(A.measure);
   bool fail = false;
   for (int r0 = 0; r0 < L; r0 += 32) {
     const int t = r0 + lane;
@@ -530,10 +605,7 @@ __device__ __forceinline__ bool score_chunk(const ScanArgs& A, const Thresh& T, 
     bool pass = false;
     if (live) {
       ++n_cand;
-      const u64 dc = dc_needed ? (u64)__ldg(A.deg + c) : 0;
-      make_key(A.measure, (u64)v, da, dc, num, den);
-      pass = !A.thr_check || key_value(A.measure, num, den, (u64)v, A.fixbits) > A.threshold;
-      if (MODE == 0 && pass && T.valid) pass = before(num, den, a, c, T.num, T.den, T.u, T.v);
+      pass = key_passes<V, MODE>(A, T, a, da, c, v, top, tcnt, num, den);
     }
     if (MODE == 0) {
       fail |= admit_global(A, pass, num, den, a, c);
@@ -559,10 +631,7 @@ __device__ __forceinline__ bool score_one(const ScanArgs& A, const Thresh& T, in
   bool pass = false;
   if (live) {
     ++n_cand;
-    const u64 dc = needs_dc(A.measure) ? (u64)__ldg(A.deg + c) : 0;
-    make_key(A.measure, (u64)v, da, dc, num, den);
-    pass = !A.thr_check || key_value(A.measure, num, den, (u64)v, A.fixbits) > A.threshold;
-    if (MODE == 0 && pass && T.valid) pass = before(num, den, a, c, T.num, T.den, T.u, T.v);
+    pass = key_passes<V, MODE>(A, T, a, da, c, v, top, tcnt, num, den);
   }
   if (MODE == 0) return admit_global(A, pass, num, den, a, c);
   TopEnt x;
@@ -637,6 +706,9 @@ __device__ __forceinline__ bool score_hash_chunk(const ScanArgs& A, const Thresh
 
 // Score the touched counters of 32 bitmap words [w0, w0 + 32) of a dense
 // window (words at or beyond nwords are absent), clearing counters and bits.
+// The set bits are first numbered across the warp (prefix sum of the word
+// popcounts), so every round scores 32 touched counters whatever their
+// spread over the words.
 template <typename V, int MODE>
 __device__ __forceinline__ bool score_dense_words(const ScanArgs& A, const Thresh& T, int a, u64 da,
                                                   V* dense, u32* bits, int w0, int nwords, int lg,
@@ -646,18 +718,34 @@ __device__ __forceinline__ bool score_dense_words(const ScanArgs& A, const Thres
   u32 w = 0;
   if (wi < nwords) {
     w = bits[wi];
-    bits[wi] = 0;
+    if (w) bits[wi] = 0;
   }
-  const int rounds = (int)__reduce_max_sync(FULLMASK, (u32)__popc(w));
+  const int cnt = __popc(w);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(FULLMASK, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int L = __shfl_sync(FULLMASK, incl, 31);
+  const int excl = incl - cnt;
   bool fail = false;
-  for (int r = 0; r < rounds; ++r) {
+  for (int r0 = 0; r0 < L; r0 += 32) {  // warp-uniform trips
+    const int t = r0 + lane;
+    // owner: the last lane j with excl_j <= t (it has a set bit when t < L)
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int e = __shfl_sync(FULLMASK, excl, j + step);
+      if (e <= t) j += step;
+    }
+    const u32 wj = __shfl_sync(FULLMASK, w, j);
+    const int ej = __shfl_sync(FULLMASK, excl, j);
     bool live = false;
     int c = 0;
     V v = 0;
-    if (w) {
-      const int bit = __ffs(w) - 1;
-      w &= w - 1;
-      const int i = wi * 32 + bit;
+    if (t < L) {
+      const int i = (w0 + j) * 32 + nth_set_bit(wj, t - ej);
       v = dense[i];
       dense[i] = 0;
       c = lg + i;
@@ -754,7 +842,7 @@ __global__ void __launch_bounds__(kWarpTierThreads) k_scan_warp(ScanArgs A, cons
             s = t.y - t.z;
             len = t.z;
           }
-          if (len > 0) w = arc_weight<V>(A.measure, t.z, A.fixbits);
+          if (len > 0) w = arc_weight<V>(A, t.z);
         }
       }
       scan_arcs<V>(s, len, w, A.idx, [&](int c, V wc) {
@@ -875,13 +963,13 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 8)) k_scan_cta(
           }
           s = s0;
           len = s1 - s0;
-          if (len > 0) w = arc_weight<V>(A.measure, t.z, A.fixbits);
+          if (len > 0) w = arc_weight<V>(A, t.z);
         }
       }
       if (is_dense) {
         scan_arcs<V>(s, len, w, A.idx, [&](int c, V wc) {
           if (MODE == 1 && c == a) return;
-          atomicAdd(&dense[c - lo], wc);
+          shared_add<V>(&dense[c - lo], wc);
         });
       } else {
         scan_arcs<V>(s, len, w, A.idx, [&](int c, V wc) {
@@ -991,50 +1079,14 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 8)) k_scan_cta(
 
 // ------------------------------------------------------------ large tier ---
 
-constexpr int kBigCursors = 2048;  // per-arc cursors kept across dense windows
-constexpr int kBigQueue = 768;     // long segments shared by all warps
-constexpr int kLongSeg = 64;       // segments at least this long are shared
-constexpr int kPiece = 256;        // wedges per shared piece
-
-constexpr int kFewArcs = 256;     // up to this many arcs: one arc per warp
-constexpr int kQueueSeg = 256;    // one-arc-per-warp mode: longer segments are shared
-
-// First index in idx[l, r) whose value is >= key; the whole warp searches
-// (32 probes per step, so about log32(r - l) dependent loads).  Warp-uniform
-// arguments; every lane returns the result.
-__device__ __forceinline__ int warp_lower_bound(const int* __restrict__ idx, int l, int r, int key) {
-  const int lane = lane_id();
-  while (r - l > 32) {
-    const int step = (r - l + 31) >> 5;
-    const int p = l + lane * step;
-    const bool lt = p < r && __ldg(idx + p) < key;
-    const int cnt = __popc(__ballot_sync(FULLMASK, lt));
-    if (cnt == 0) return l;
-    const int nl = l + (cnt - 1) * step + 1;
-    const int nr = min(r, l + cnt * step);
-    l = nl;
-    r = nr;
-  }
-  const int p = l + lane;
-  const bool lt = p < r && __ldg(idx + p) < key;
-  return l + __popc(__ballot_sync(FULLMASK, lt));
-}
-
-// The warp streams one segment idx[0, len) with eight loads per lane in
-// flight, calling f(c, w) for each id.
-template <typename V, typename F>
-__device__ __forceinline__ void stream_segment(const int* __restrict__ p, int len, V w, F&& f) {
-  const int lane = lane_id();
-  int i = lane;
-  for (; i + 224 < len; i += 256) {
-    int c[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) c[j] = __ldg(p + i + 32 * j);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) f(c[j], w);
-  }
-  for (; i < len; i += 32) f(__ldg(p + i), w);
-}
+// Shared memory of a large-tier CTA of THREADS threads beyond its table
+// (big_extra_smem(THREADS) bytes): a window-boundary table of
+// big_bounds(THREADS) positions, then a queue of THREADS long segments
+// (length / wedge prefix, start, weight).
+__host__ __device__ constexpr int big_bounds(int threads) { return 4 * threads; }
+constexpr int kPiece = 256;  // wedges per piece: eight per lane
+constexpr int kLongSeg = 64; // segments at least this long are shared as pieces
+constexpr int kShortSeg = 8; // the same when the item has at most one arc per thread
 
 // First index in idx[l, r) whose value is >= key, searching outward from l.
 __device__ __forceinline__ int lower_bound_gallop(const int* __restrict__ idx, int l, int r,
@@ -1050,37 +1102,88 @@ __device__ __forceinline__ int lower_bound_gallop(const int* __restrict__ idx, i
   }
 }
 
-// One 32-warp CTA per item.  A hash item is one vertex range; a dense item
-// sweeps G consecutive windows of at most A.big_span vertices, carrying each
-// arc's position from window to window (no repeated binary search).  In every
-// range, segments of kLongSeg or more wedges are cut into kPiece-wedge pieces
-// that all warps share, so a source with a few long intermediary lists still
-// keeps every warp busy.
-template <bool V64, int MODE>
-__global__ void __launch_bounds__(kCtaThreads, 1) k_scan_big(ScanArgs A, const int4* __restrict__ q,
-                                                             u64 nq, int table_bytes,
-                                                             u64* __restrict__ claim) {
+// Exclusive CTA-wide prefix sums of two ints per thread (ex, ey) and their
+// totals (tx, ty).  One barrier; wtot (one int2 per warp) must not be written
+// again before every thread has passed a later barrier.
+template <int THREADS>
+__device__ __forceinline__ void block_scan2(int x, int y, int& ex, int& ey, int& tx, int& ty,
+                                            int2* wtot) {
+  constexpr int NW = THREADS / 32;
+  const int lane = lane_id();
+  const int wid = threadIdx.x >> 5;
+  int ix = x, iy = y;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int ux = __shfl_up_sync(FULLMASK, ix, o);
+    const int uy = __shfl_up_sync(FULLMASK, iy, o);
+    if (lane >= o) {
+      ix += ux;
+      iy += uy;
+    }
+  }
+  if (lane == 31) wtot[wid] = make_int2(ix, iy);
+  __syncthreads();
+  const int2 t = lane < NW ? wtot[lane] : make_int2(0, 0);
+  int sx = t.x, sy = t.y;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int ux = __shfl_up_sync(FULLMASK, sx, o);
+    const int uy = __shfl_up_sync(FULLMASK, sy, o);
+    if (lane >= o) {
+      sx += ux;
+      sy += uy;
+    }
+  }
+  ex = __shfl_sync(FULLMASK, sx - t.x, wid) + ix - x;
+  ey = __shfl_sync(FULLMASK, sy - t.y, wid) + iy - y;
+  tx = __shfl_sync(FULLMASK, sx, NW - 1);
+  ty = __shfl_sync(FULLMASK, sy, NW - 1);
+}
+
+// Last j in [lo, hi) with p[j] <= key (p ascending, p[lo] <= key).
+__device__ __forceinline__ int last_le(const int* p, int lo, int hi, int key) {
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (p[mid] <= key) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// One CTA per item.  A hash item is one vertex range; a dense item sweeps G
+// consecutive windows of at most A.big_span vertices.  Each arc's segment (the
+// part of its suffix inside the range) comes from a boundary table filled once
+// per item when it fits (independent binary searches, one per thread), from a
+// cursor carried between windows, or from a binary search.  Warps take 32 arcs
+// at a time and walk the short segments at once; segments of kLongSeg or more
+// wedges are queued, laid end to end by a CTA prefix sum and dealt to all
+// warps in pieces of kPiece wedges, so a source with a few long intermediary
+// lists still keeps every warp busy.
+template <bool V64, int MODE, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A, const int4* __restrict__ q,
+                                                                      u64 nq, int table_bytes,
+                                                                      u64* __restrict__ claim) {
   typedef typename std::conditional<V64, u64, u32>::type V;
-  constexpr int NW = kCtaThreads / 32;
+  constexpr int NW = THREADS / 32;
+  constexpr int NB = big_bounds(THREADS);
   extern __shared__ __align__(16) unsigned char smem[];
   const int max_slots = 1 << (ceil_log2((u64)table_bytes / (4 + sizeof(V)) + 1) - 1);
   int* keys = reinterpret_cast<int*>(smem);
   V* vals = reinterpret_cast<V*>(smem + (size_t)max_slots * 4);
   V* dense = reinterpret_cast<V*>(smem);
   u32* dbits = reinterpret_cast<u32*>(smem + (size_t)A.big_span * sizeof(V));  // touched bits
-  int* cursors = reinterpret_cast<int*>(smem + table_bytes);
-  int* q_s = cursors + kBigCursors;
-  int* q_len = q_s + kBigQueue;
-  int* q_pref = q_len + kBigQueue;
-  u64* q_w = reinterpret_cast<u64*>(q_pref + kBigQueue);
-  TopEnt* tops = reinterpret_cast<TopEnt*>(q_w + kBigQueue);
+  int* bnd = reinterpret_cast<int*>(smem + table_bytes);  // boundaries or cursors
+  int* c_p = bnd + NB;                                    // queued segment: length, then prefix
+  int* c_s = c_p + THREADS;                               // start, then start - prefix
+  u64* c_w = reinterpret_cast<u64*>(c_s + THREADS);       // weight
+  TopEnt* tops = reinterpret_cast<TopEnt*>(c_w + THREADS);
   __shared__ int4 s_rec;
   __shared__ u64 s_next;
-  __shared__ int s_ndistinct, s_overflow, s_fail, s_qn, s_qpieces, s_qhead;
+  __shared__ int s_ndistinct, s_overflow, s_fail, s_qn;
   __shared__ int s_tcnt[NW];
-  // optional phase profile (thread 0's clock): 0 item setup, 1 own arcs,
-  // 2 wait for the other warps' arcs, 3 shared pieces, 4 exclusion + scoring,
-  // 5 item end
+  __shared__ int2 s_wtot[NW];
+  // optional phase profile (thread 0's clock): 0 item setup and boundary
+  // table, 1 segment bounds and prefix sum, 2 unused, 3 pieces, 4 exclusion
+  // and scoring, 5 item end
   long long t_prof[6] = {0, 0, 0, 0, 0, 0};
   long long t_last = clock64();
   const bool prof = A.prof != nullptr && threadIdx.x == 0;
@@ -1095,7 +1198,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_scan_big(ScanArgs A, const i
 
   const int lane = lane_id();
   const int wid = threadIdx.x >> 5;
-  for (int i = threadIdx.x * 16; i < table_bytes; i += kCtaThreads * 16)
+  for (int i = threadIdx.x * 16; i < table_bytes; i += THREADS * 16)
     *reinterpret_cast<int4*>(smem + i) = make_int4(0, 0, 0, 0);
   Thresh T;
   if (MODE == 0) T = *A.thresh;
@@ -1128,9 +1231,24 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_scan_big(ScanArgs A, const i
     const int limit = (nslots * 3) / 4;
     const int span = hi - lo;
     const int e0 = A.off[a], e1 = A.off[a + 1];
-    const bool use_cur = G > 1 && (e1 - e0) <= kBigCursors;
-    const bool few_arcs = (e1 - e0) <= kFewArcs;
-    const u64 da = (u64)(e1 - e0);
+    const int K = e1 - e0;
+    // dense sweeps: all window boundaries of every arc up front when they
+    // fit (independent binary searches, one per thread), else a cursor per
+    // arc carried from window to window
+    const bool pre = G > 1 && (long long)K * (G + 1) <= NB;
+    const bool use_cur = G > 1 && !pre && K <= NB;
+    if (pre) {
+      for (int q2 = threadIdx.x; q2 < K * (G + 1); q2 += THREADS) {
+        const int j = q2 / (G + 1);
+        const int gg = q2 - j * (G + 1);
+        const Arc t = A.arc[e0 + j];
+        const int s0 = MODE ? t.y - t.z : t.x + 1;
+        const int key = lo + (int)(((u64)span * (u64)gg) / (u64)G);
+        bnd[q2] = (t.z <= A.cap && s0 < t.y) ? lower_bound_g(A.idx, s0, t.y, key) : s0;
+      }
+      __syncthreads();
+    }
+    const u64 da = (u64)K;
     TopEnt* top = tops + wid * (MODE ? A.k : 0);
     int tcnt = 0;
     bool fail = false;
@@ -1143,7 +1261,6 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_scan_big(ScanArgs A, const i
         s_ndistinct = 0;
         s_overflow = 0;
         s_qn = 0;
-        s_qhead = 0;
       }
       __syncthreads();
       LP_PHASE(0);
@@ -1151,7 +1268,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_scan_big(ScanArgs A, const i
         if (MODE == 1 && c == a) return;
         if (is_dense) {
           const int i = c - lg;
-          if (atomicAdd(&dense[i], wc) == 0) atomicOr(&dbits[i >> 5], 1u << (i & 31));
+          // the first add sees a zero low word (a later wrap to zero only
+          // sets the bit again)
+          if (shared_add<V>(&dense[i], wc) == 0) atomicOr(&dbits[i >> 5], 1u << (i & 31));
         } else {
           if (*(volatile int*)&s_overflow) return;
           const int rc = hash_add<V>(keys, vals, logcap, c, wc);
@@ -1162,144 +1281,90 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_scan_big(ScanArgs A, const i
           }
         }
       };
-      // phase 1 (few arcs): one arc per warp, bounds found by warp-wide
-      // searches, the segment streamed by the warp (the longest are queued)
-      if (few_arcs) {
-        for (int e = e0 + wid; e < e1; e += NW) {
-          const Arc t = A.arc[e];
-          if (t.z > A.cap) continue;  // warp-uniform
-          int s0, s1;
-          if (MODE == 0) {
-            s0 = t.x + 1;
-            s1 = t.y;
-          } else {
-            s0 = t.y - t.z;
-            s1 = t.y;
-          }
-          if (!full_range && s0 < s1) {
-            const int st = (use_cur && g > 0) ? cursors[e - e0] : warp_lower_bound(A.idx, s0, s1, lg);
-            const int en = warp_lower_bound(A.idx, st, s1, hg);
-            if (use_cur && lane == 0) cursors[e - e0] = en;
-            s0 = st;
-            s1 = en;
-          }
-          const int len = s1 - s0;
-          if (len <= 0) continue;
-          const V w = arc_weight<V>(A.measure, t.z, A.fixbits);
-          if (len >= kQueueSeg) {
-            int slot = 0;
-            if (lane == 0) slot = atomicAdd(&s_qn, 1);
-            slot = __shfl_sync(FULLMASK, slot, 0);
-            if (slot < kBigQueue) {
-              if (lane == 0) {
-                q_s[slot] = s0;
-                q_len[slot] = len;
-                q_w[slot] = (u64)w;
-              }
-              continue;
-            }
-          }
-          stream_segment<V>(A.idx + s0, len, w, insert);
-          if (!is_dense && __any_sync(FULLMASK, *(volatile int*)&s_overflow != 0)) break;
-        }
-      }
-      // phase 1 (many arcs): each warp takes 32 arcs at a time; long
-      // segments are queued
-      for (int eb = e0 + wid * 32; !few_arcs && eb < e1; eb += NW * 32) {
-        const int e = eb + lane;
-        int s = 0, len = 0;
+      // phase A: each warp takes 32 arcs at a time, one per lane; short
+      // segments are walked at once (concatenated across the lanes), longer
+      // ones are queued for phase B.  With fewer arcs than threads most warps
+      // hold no arc, so all but the shortest segments are queued.
+      const int long_seg = K <= THREADS ? kShortSeg : kLongSeg;
+      for (int eb = wid * 32; eb < K; eb += NW * 32) {  // warp-uniform trips
+        const int j = eb + lane;
+        int st = 0, len = 0;
         V w = 0;
-        if (e < e1) {
-          const Arc t = A.arc[e];
+        if (j < K) {
+          const Arc t = A.arc[e0 + j];
           if (t.z <= A.cap) {
-            int s0, s1;
-            if (MODE == 0) {
-              s0 = t.x + 1;
-              s1 = t.y;
-            } else {
-              s0 = t.y - t.z;
-              s1 = t.y;
+            int s0 = MODE ? t.y - t.z : t.x + 1, s1 = t.y;
+            if (s0 < s1) {
+              if (pre) {
+                s0 = bnd[j * (G + 1) + g];
+                s1 = bnd[j * (G + 1) + g + 1];
+              } else if (!full_range) {
+                const int b0 = (use_cur && g > 0) ? bnd[j] : lower_bound_g(A.idx, s0, s1, lg);
+                const int b1 = use_cur ? lower_bound_gallop(A.idx, b0, s1, hg)
+                                       : lower_bound_g(A.idx, b0, s1, hg);
+                if (use_cur) bnd[j] = b1;
+                s0 = b0;
+                s1 = b1;
+              }
             }
-            if (!full_range && s0 < s1) {
-              const int st = (use_cur && g > 0) ? cursors[e - e0] : lower_bound_g(A.idx, s0, s1, lg);
-              const int en = use_cur ? lower_bound_gallop(A.idx, st, s1, hg)
-                                     : lower_bound_g(A.idx, st, s1, hg);
-              if (use_cur) cursors[e - e0] = en;
-              s0 = st;
-              s1 = en;
-            }
-            s = s0;
-            len = s1 - s0;
-            if (len > 0) w = arc_weight<V>(A.measure, t.z, A.fixbits);
+            st = s0;
+            len = s1 > s0 ? s1 - s0 : 0;
+            if (len > 0) w = arc_weight<V>(A, t.z);
           }
         }
-        if (len >= kLongSeg) {
+        if (len >= long_seg) {
           const int slot = atomicAdd(&s_qn, 1);
-          if (slot < kBigQueue) {
-            q_s[slot] = s;
-            q_len[slot] = len;
-            q_w[slot] = (u64)w;
+          if (slot < THREADS) {  // else the warp walks it below
+            c_s[slot] = st;
+            c_p[slot] = len;
+            c_w[slot] = (u64)w;
             len = 0;
           }
         }
-        scan_arcs<V>(s, len, w, A.idx, insert);
+        scan_arcs<V>(st, len, w, A.idx, insert);
         if (!is_dense && __any_sync(FULLMASK, *(volatile int*)&s_overflow != 0)) break;
       }
-      LP_PHASE(1);
       __syncthreads();
-      LP_PHASE(2);
-      // phase 2: shared pieces of the queued long segments
-      const int nqd = min(s_qn, kBigQueue);
-      if (nqd > 0) {
-        if (wid == 0) {
-          int carry = 0;
-          for (int b0 = 0; b0 < nqd; b0 += 32) {
-            const int i = b0 + lane;
-            const int pc = i < nqd ? (q_len[i] + kPiece - 1) / kPiece : 0;
-            int incl = pc;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const int t = __shfl_up_sync(FULLMASK, incl, o);
-              if (lane >= o) incl += t;
-            }
-            if (i < nqd) q_pref[i] = carry + incl - pc;
-            carry += __shfl_sync(FULLMASK, incl, 31);
-          }
-          if (lane == 0) s_qpieces = carry;
+      LP_PHASE(1);
+      // phase B: the queued segments end to end, dealt to the warps in
+      // pieces of kPiece wedges
+      const int nqd = min(s_qn, THREADS);
+      if (nqd > 0 && (is_dense || !s_overflow)) {  // CTA-uniform
+        const int len = threadIdx.x < nqd ? c_p[threadIdx.x] : 0;
+        int ex, unused, tot, unused2;
+        block_scan2<THREADS>(len, 0, ex, unused, tot, unused2, s_wtot);
+        if (threadIdx.x < nqd) {
+          c_p[threadIdx.x] = ex;
+          c_s[threadIdx.x] -= ex;
         }
         __syncthreads();
-        const int npieces = s_qpieces;
-        for (;;) {
-          int p = 0;
-          if (lane == 0) p = atomicAdd(&s_qhead, 1);
-          p = __shfl_sync(FULLMASK, p, 0);
-          if (p >= npieces) break;
-          int l2 = 0, h2 = nqd - 1;  // last segment with q_pref <= p
-          while (l2 < h2) {
-            const int m = (l2 + h2 + 1) >> 1;
-            if (q_pref[m] <= p) l2 = m; else h2 = m - 1;
+        for (int p = wid; p * kPiece < tot; p += NW) {  // warp-uniform trips
+          const int i0 = p * kPiece + lane;
+          int jj = i0 < tot ? last_le(c_p, 0, nqd, i0) : 0;
+          int c8[8], j8[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int i = i0 + 32 * u;
+            c8[u] = -1;
+            if (i < tot) {
+              // i - 32 lay in segment jj and segments are not empty, so i
+              // lies in one of the segments jj .. jj + 32
+              if (jj + 1 < nqd && c_p[jj + 1] <= i) jj = last_le(c_p, jj + 1, min(nqd, jj + 33), i);
+              c8[u] = __ldg(A.idx + c_s[jj] + i);
+              j8[u] = jj;
+            }
           }
-          const int off = (p - q_pref[l2]) * kPiece;
-          const int plen = min(kPiece, q_len[l2] - off);
-          const int* src = A.idx + q_s[l2] + off;
-          const V wj = (V)q_w[l2];
-          int i = lane;
-          for (; i + 96 < plen; i += 128) {
-            const int c0 = __ldg(src + i), c1 = __ldg(src + i + 32), c2 = __ldg(src + i + 64),
-                      c3 = __ldg(src + i + 96);
-            insert(c0, wj);
-            insert(c1, wj);
-            insert(c2, wj);
-            insert(c3, wj);
-          }
-          for (; i < plen; i += 32) insert(__ldg(src + i), wj);
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (c8[u] >= 0) insert(c8[u], (V)c_w[j8[u]]);
+          if (!is_dense && __any_sync(FULLMASK, *(volatile int*)&s_overflow != 0)) break;
         }
         __syncthreads();
       }
       LP_PHASE(3);
       if (!is_dense && s_overflow) {
         // give the range back for splitting; leave the table empty
-        for (int i = threadIdx.x * 4; i < nslots; i += kCtaThreads * 4) {
+        for (int i = threadIdx.x * 4; i < nslots; i += THREADS * 4) {
           *reinterpret_cast<int4*>(keys + i) = make_int4(0, 0, 0, 0);
           zero4<V>(vals + i);
         }
@@ -1308,7 +1373,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_scan_big(ScanArgs A, const i
         break;  // hash items have a single range
       }
       // drop first-order neighbours inside [lg, hg)
-      for (int e = e0 + threadIdx.x; e < e1; e += kCtaThreads) {
+      for (int e = e0 + threadIdx.x; e < e1; e += THREADS) {
         const int b = __ldg(A.idx + e);
         if (b < lg || b >= hg || (MODE == 0 && b <= a)) continue;
         if (is_dense) dense[b - lg] = 0;
@@ -1318,11 +1383,11 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_scan_big(ScanArgs A, const i
       // score and select: touched counters (dense) or packed live slots (hash)
       if (is_dense) {
         const int nwords = (hg - lg + 31) >> 5;
-        for (int w0 = wid * 32; w0 < nwords; w0 += kCtaThreads)  // warp-uniform trips
+        for (int w0 = wid * 32; w0 < nwords; w0 += THREADS)  // warp-uniform trips
           fail |= score_dense_words<V, MODE>(A, T, a, da, dense, dbits, w0, nwords, lg, top, tcnt,
                                              n_cand);
       } else {
-        for (int base0 = wid * 128; base0 < nslots; base0 += kCtaThreads * 4)
+        for (int base0 = wid * 128; base0 < nslots; base0 += THREADS * 4)
           fail |= score_hash_chunk<V, MODE>(A, T, a, da, keys, vals, base0, nslots, top, tcnt,
                                             n_cand);
       }
@@ -1556,6 +1621,23 @@ static int num_sms() {
   return g_nsm;
 }
 
+// Allow kern the device's whole opt-in shared memory.  The value is the same
+// on every call, so threads launching it concurrently with different dynamic
+// sizes cannot race on the attribute (a smaller size set by one thread would
+// make another thread's larger launch fail).
+template <typename Kern>
+static cudaError_t allow_max_smem(Kern kern) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  int dev = 0, optin = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+
 cudaError_t launch_estimate2(const ScanArgs& A, int n_rec, int4* warpq, int4* medq, int4* itemq,
                              u64 itemq_cap, int2* grp, cudaStream_t st) {
   if (n_rec <= 0) return cudaSuccess;
@@ -1580,7 +1662,7 @@ static cudaError_t launch_warp_t(const ScanArgs& A, const int4* q, u64 nq, cudaS
   const size_t smem = (size_t)nw * kWarpSlots * (4 + sizeof(V)) +
                       (MODE ? (size_t)nw * A.k * sizeof(TopEnt) : 0);
   auto kern = k_scan_warp<V64, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(kern);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpTierThreads, smem);
@@ -1604,7 +1686,7 @@ static cudaError_t launch_cta_t(const ScanArgs& A, const int4* q, u64 nq, int ta
                                 u64* claim, cudaStream_t st) {
   const size_t smem = (size_t)table_bytes + (MODE ? (size_t)(THREADS / 32) * A.k * sizeof(TopEnt) : 0);
   auto kern = k_scan_cta<V64, MODE, THREADS>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(kern);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
@@ -1615,24 +1697,36 @@ static cudaError_t launch_cta_t(const ScanArgs& A, const int4* q, u64 nq, int ta
   return cudaGetLastError();
 }
 
-template <bool V64, int MODE>
+template <bool V64, int MODE, int THREADS>
 static cudaError_t launch_big_t(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st) {
+  static_assert(big_extra_smem(THREADS) == big_bounds(THREADS) * 4 + THREADS * (4 + 4 + 8),
+                "large-tier shared memory layout");
   const int tb = A.big_bytes;
-  const size_t smem = (size_t)tb + kBigExtraSmem +
-                      (MODE ? (size_t)(kCtaThreads / 32) * A.k * sizeof(TopEnt) : 0);
-  auto kern = k_scan_big<V64, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = (size_t)tb + big_extra_smem(THREADS) +
+                      (MODE ? (size_t)(THREADS / 32) * A.k * sizeof(TopEnt) : 0);
+  auto kern = k_scan_big<V64, MODE, THREADS>;
+  cudaError_t e = allow_max_smem(kern);
   if (e != cudaSuccess) return e;
-  const int blocks = (int)max((u64)1, min((u64)num_sms(), nq));
-  kern<<<blocks, kCtaThreads, smem, st>>>(A, q, nq, tb, &A.ctr->claim_c);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int blocks = (int)max((u64)1, min((u64)num_sms() * per_sm, nq));
+  kern<<<blocks, THREADS, smem, st>>>(A, q, nq, tb, &A.ctr->claim_c);
   return cudaGetLastError();
+}
+
+template <bool V64, int MODE>
+static cudaError_t launch_big_v(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st) {
+  if (A.big_threads == 512) return launch_big_t<V64, MODE, 512>(A, q, nq, st);
+  return launch_big_t<V64, MODE, 1024>(A, q, nq, st);
 }
 
 cudaError_t launch_scan_cta(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st) {
   if (nq == 0) return cudaSuccess;
   const bool v64 = A.measure == LP_AA || A.measure == LP_RA;
-  if (A.mode == 0) return v64 ? launch_big_t<true, 0>(A, q, nq, st) : launch_big_t<false, 0>(A, q, nq, st);
-  return v64 ? launch_big_t<true, 1>(A, q, nq, st) : launch_big_t<false, 1>(A, q, nq, st);
+  if (A.mode == 0) return v64 ? launch_big_v<true, 0>(A, q, nq, st) : launch_big_v<false, 0>(A, q, nq, st);
+  return v64 ? launch_big_v<true, 1>(A, q, nq, st) : launch_big_v<false, 1>(A, q, nq, st);
 }
 
 cudaError_t launch_scan_med(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st) {

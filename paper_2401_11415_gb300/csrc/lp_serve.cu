@@ -32,6 +32,7 @@ struct Request {
   std::vector<lp_link> out;
   std::vector<int32_t> counts;
   lp_status status = LP_OK;
+  std::string error;  // the worker's error text when status != LP_OK
   bool done = false;
 };
 
@@ -111,7 +112,7 @@ void worker_main(lp_server* S, int si) {
     cudaStream_t st = slot.shadow->stream;
     lp_status status = LP_OK;
     cudaError_t e = cudaMemcpyAsync(slot.d_src, slot.h_src, sizeof(int) * n, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) status = LP_ECUDA;
+    if (e != cudaSuccess) status = lp::report_cuda(e, "serving: source upload");
     if (status == LP_OK)
       status = lp::run_sources_dev(*slot.shadow, batch[0]->measure, batch[0]->cap, slot.d_src, n, k,
                                    0.0, slot.d_out, slot.d_cnt);
@@ -121,8 +122,9 @@ void worker_main(lp_server* S, int si) {
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(slot.h_cnt, slot.d_cnt, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) status = LP_ECUDA;
+      if (e != cudaSuccess) status = lp::report_cuda(e, "serving: result download");
     }
+    const std::string error = status == LP_OK ? std::string() : std::string(lp_last_error());
     int off = 0;
     for (Request* r : batch) {
       const size_t m = r->sources.size();
@@ -131,6 +133,7 @@ void worker_main(lp_server* S, int si) {
         r->counts.assign(slot.h_cnt + off, slot.h_cnt + off + m);
       }
       r->status = status;
+      r->error = error;
       off += (int)m;
     }
     {
@@ -251,8 +254,9 @@ lp_status lp_serve_wait(lp_server* S, uint64_t req_id, int64_t timeout_us, lp_li
     if (out) std::memcpy(out, r->out.data(), sizeof(lp_link) * r->out.size());
     if (counts) std::memcpy(counts, r->counts.data(), sizeof(int32_t) * r->counts.size());
   }
+  const std::string msg = "lp_serve_wait: the request's batch failed: " + r->error;
   delete r;
-  if (st != LP_OK) return serve_fail(st, "lp_serve_wait: the request's batch failed");
+  if (st != LP_OK) return serve_fail(st, msg.c_str());
   return LP_OK;
 }
 

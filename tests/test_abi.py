@@ -51,6 +51,10 @@ def test_version_and_options(lp):
     with pytest.raises(lp.LPError) as e:
         lp.lp_set_option(lp.LP_OPT_WARP_MAX_WEDGES, 100000)
     assert e.value.status == lp.LP_EINVAL
+    assert lp.lp_get_option(lp.LP_OPT_BIG_CTA_THREADS) == 1024
+    with pytest.raises(lp.LPError) as e:
+        lp.lp_set_option(lp.LP_OPT_BIG_CTA_THREADS, 768)
+    assert e.value.status == lp.LP_EINVAL
     assert lp.lp_get_option(99) == -1
 
 

@@ -170,15 +170,18 @@ def test_compaction_and_redo(lp, cfg1):
         lp.lp_set_option(lp.LP_OPT_SELECT_BUFFER, old)
 
 
-def test_split_and_dense_items(lp):
+@pytest.mark.parametrize("big_threads", [1024, 512])
+def test_split_and_dense_items(lp, big_threads):
     """Tiny tier limits and split tables force CTA items, hash overflows that
-    are re-split, and dense-counter items."""
+    are re-split, and dense-counter items; with one 1024-thread or two
+    512-thread large-tier CTAs per SM (half the table, half the window)."""
     g = L.chung_lu(3000, 12.0, 2.05, dmax=1500, seed=12)
     keys = (lp.LP_OPT_WARP_MAX_WEDGES, lp.LP_OPT_MED_MAX_WEDGES, lp.LP_OPT_CTA_MAX_WEDGES,
-            lp.LP_OPT_SPLIT_TARGET, lp.LP_OPT_SPLIT_LOGCAP)
+            lp.LP_OPT_SPLIT_TARGET, lp.LP_OPT_SPLIT_LOGCAP, lp.LP_OPT_BIG_CTA_THREADS)
     old = [lp.lp_get_option(x) for x in keys]
     try:
         for vals in ((8, 16, 257, 256, 6), (64, 512, 1024, 2048, 9), (256, 1024, 8192, 6144, 14)):
+            vals = vals + (big_threads,)
             for x, v in zip(keys, vals):
                 lp.lp_set_option(x, v)
             for m in ("CN", "JC", "RA", "AA"):
