@@ -110,8 +110,11 @@ typedef struct {
   int32_t tier_launches[3];/* launches of the tier's scan kernel             */
   float tier_ms[3];        /* summed device time of those launches (timing on) */
   int64_t phase_cycles[6]; /* LP_OPT_PHASE_PROFILE: SM cycles of the large tier
-                              (summed over CTAs) in item setup, own arcs, shared
-                              pieces, exclusion, scoring, item end            */
+                              (summed over CTAs) in [0] item setup, [1] arc
+                              segments and short walks, [3] long-segment
+                              pieces, [4] exclusion and scoring, [5] item end;
+                              [2] is the whole time of dense items (also in
+                              the others)                                     */
 } lp_stats;
 
 /*

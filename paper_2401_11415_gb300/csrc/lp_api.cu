@@ -129,7 +129,7 @@ static void free_graph(Graph* g) {
   Graph::Scratch* all[] = {&g->s_ctr, &g->s_w, &g->s_warpq, &g->s_itemq, &g->s_warpq2,
                            &g->s_itemq2, &g->s_medq, &g->s_medq2, &g->s_buf, &g->s_buf2,
                            &g->s_buf3, &g->s_misc, &g->s_failed, &g->s_split,
-                           &g->s_thresh, &g->s_flags, &g->s_partial, &g->s_phdr, &g->s_top,
+                           &g->s_thresh, &g->s_vfloor, &g->s_flags, &g->s_partial, &g->s_phdr, &g->s_top,
                            &g->s_cnt, &g->s_links, &g->s_src, &g->s_grp};
   for (auto* s : all)
     if (s->p) cudaFree(s->p);
@@ -388,10 +388,14 @@ struct Queues {
 };
 
 // Launch the scan kernels; with timing on, time each on the graph's stream.
-static cudaError_t scan_launches(Graph& g, const ScanArgs& A, const Queues& Q, bool timing) {
+// Launch the scan of the tiers in `tiers` (bit t: tier t), smallest sources
+// first: in the global mode their candidates are the first to reach the
+// selection buffer, and they tend to rank high (few neighbours, high overlap).
+static cudaError_t scan_launches(Graph& g, const ScanArgs& A, const Queues& Q, bool timing,
+                                 int tiers = 7) {
   cudaStream_t st = g.stream;
-  for (int t = 2; t >= 0; --t) {  // largest work first
-    if (!Q.n[t]) continue;
+  for (int t = 0; t < 3; ++t) {
+    if (!Q.n[t] || !(tiers & (1 << t))) continue;
     if (timing) cudaEventRecord(g.kev[2 * t], st);
     const int4* q = sp<int4>(*Q.cur[t]);
     cudaError_t e = t == 0 ? launch_scan_warp(A, q, Q.n[t], st)
@@ -406,11 +410,12 @@ static cudaError_t scan_launches(Graph& g, const ScanArgs& A, const Queues& Q, b
 }
 
 // After the stream synchronised: add the kernels' event times to the stats.
-static void scan_times(Graph& g, const Queues& Q, bool timing) {
+static void scan_times(Graph& g, const Queues& Q, bool timing, int tiers = 7) {
   if (!timing) return;
   for (int t = 0; t < 3; ++t) {
     float ms = 0.f;
-    if (Q.n[t] && cudaEventElapsedTime(&ms, g.kev[2 * t], g.kev[2 * t + 1]) == cudaSuccess)
+    if (Q.n[t] && (tiers & (1 << t)) &&
+        cudaEventElapsedTime(&ms, g.kev[2 * t], g.kev[2 * t + 1]) == cudaSuccess)
       t_stats.tier_ms[t] += ms;
   }
 }
@@ -451,8 +456,10 @@ static ScanArgs base_args(Graph& g, int measure, int cap, double threshold, int 
   while ((2ll << big_logcap) * (4 + vbytes) <= big_bytes) ++big_logcap;
   A.big_bytes = big_bytes;
   A.big_logcap = big_logcap;
-  // dense window: counters plus one touched bit per counter, 128-aligned
-  A.big_span = (int)(((long long)big_bytes * 8 / (8 * vbytes + 1)) & ~127ll);
+  // dense window (128-aligned): in the global mode counters only (scored by
+  // a linear scan), in the per-source mode counters plus one touched bit each
+  A.big_span = mode == 0 ? (int)(((long long)big_bytes / vbytes) & ~127ll)
+                         : (int)(((long long)big_bytes * 8 / (8 * vbytes + 1)) & ~127ll);
   A.warp_max = std::min(o.warp_max, kWarpMaxWedges);
   A.med_max = std::max(A.warp_max, std::min(o.med_max, kMedMaxWedges));
   A.cta_max = std::max(A.med_max, std::min(o.cta_max, 1 << (big_logcap - 1)));
@@ -617,6 +624,7 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
   const u64 failed_cap = 1 << 20, split_cap = 1 << 20;
   CU(ensure(g, g.s_ctr, sizeof(Counters)));
   CU(ensure(g, g.s_thresh, sizeof(Thresh)));
+  CU(ensure(g, g.s_vfloor, sizeof(u64) * ((size_t)g.dmax + 1)));
   CU(ensure(g, g.s_buf, sizeof(Cand) * C));
   CU(ensure(g, g.s_buf2, sizeof(Cand) * C));
   CU(ensure(g, g.s_buf3, sizeof(Cand) * C));
@@ -648,15 +656,19 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
     A.buf = sp<Cand>(g.s_buf);
     A.buf_cap = C;
     A.thresh = d_th;
+    A.vfloor = sp<u64>(g.s_vfloor);
     A.failed = sp<int4>(g.s_failed);
     A.failed_cap = failed_cap;
     A.split = sp<int4>(g.s_split);
     A.split_cap = split_cap;
     A.prof = options_snapshot().phase_profile ? d_ctr->prof : nullptr;
-    CU(scan_launches(g, A, Q, tm.on));
+    // first round: the warp and medium tiers alone, so that the threshold
+    // they set (a compaction below) already filters the large tier
+    const bool seed = round == 0 && k > 0 && Q.n[2] > 0 && Q.n[0] + Q.n[1] > 0;
+    CU(scan_launches(g, A, Q, tm.on, seed ? 3 : 7));
     CU(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    scan_times(g, Q, tm.on);
+    scan_times(g, Q, tm.on, seed ? 3 : 7);
     for (int i = 0; i < 6; ++i) t_stats.phase_cycles[i] += (int64_t)h.prof[i];
     if (h.error) return fail(LP_EINTERNAL, "lp_predict: device check %u", h.error);
     t_stats.candidates += (int64_t)h.candidates;
@@ -670,7 +682,7 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
                          std::min<u64>(h.claim_c, Q.n[2])};
     const u64 valid = std::min<u64>(h.cand_cnt, C);
     t_stats.splits += (int32_t)h.nsplit;
-    if (h.full) {
+    if (h.full || (seed && valid >= (u64)k)) {
       // compaction: drop failed output, then sort and cut to k
       t_stats.compactions++;
       Cand* src = sp<Cand>(g.s_buf);
@@ -704,6 +716,8 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
         // them is the threshold; SC / LHN: sorted, entry k-1 is)
         if (measure == LP_SC || measure == LP_LHN) CU(launch_set_thresh(sp<Cand>(g.s_buf), (u64)k, d_th, st));
         else CU(launch_thresh_worst(sp<Cand>(g.s_buf), (u64)k, misc_worst(g), d_th, st, &t_stats.launches));
+        CU(launch_count_floor(measure, g.dmax, d_th, sp<u64>(g.s_vfloor), st));
+        t_stats.launches += 1;
         kept = (u64)k;
       } else {
         kept = m;

@@ -29,9 +29,9 @@ constexpr int kCtaMaxWedges = 8192;      // single-item hash: W <= this
 constexpr int kSplitTarget = 6144;       // wedges per split hash item
 constexpr int kCtaSmem = 192 * 1024;     // table bytes of a 1024-thread large-tier CTA
 // shared memory of a large-tier CTA of `threads` threads beyond its table:
-// 4 * threads window boundaries (or arc cursors) and one chunk of `threads`
-// arcs (wedge prefix, segment base, weight)
-constexpr int big_extra_smem(int threads) { return threads * 4 * 4 + threads * (4 + 4 + 8); }
+// 3 * threads window boundaries (or arc cursors) and a queue of `threads`
+// segments (prefix, start, length, weight)
+constexpr int big_extra_smem(int threads) { return threads * 3 * 4 + threads * (4 + 4 + 4 + 8); }
 // shared memory the large tier may use per SM (two 512-thread CTAs share it)
 constexpr int kSmemPerSm = 228 * 1024;
 constexpr int kSmemPerCtaReserved = 1024;
@@ -110,6 +110,7 @@ struct ScanArgs {
   Cand* buf;
   u64 buf_cap;
   const Thresh* thresh;
+  const u64* vfloor;   // [dmax + 1]: count floor of a source degree under *thresh
   // failure / split records
   int4* failed;
   u64 failed_cap;
@@ -172,7 +173,7 @@ struct Graph {
   };
   Scratch s_ctr, s_w, s_warpq, s_itemq, s_warpq2, s_itemq2, s_medq, s_medq2, s_buf, s_buf2,
       s_failed, s_split, s_thresh, s_flags, s_partial, s_phdr, s_top, s_cnt, s_links, s_src, s_grp,
-      s_buf3, s_misc;
+      s_buf3, s_misc, s_vfloor;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // per kernel
 };
@@ -204,6 +205,8 @@ inline u64 sort_splits_needed(u64 n) { return n / 2048 + 2; }
 cudaError_t launch_sort_cands(Cand* d_a, Cand* d_tmp, int* splits, u64 n, cudaStream_t st,
                               Cand** result, int* launches);
 cudaError_t launch_set_thresh(const Cand* sorted, u64 k, Thresh* t, cudaStream_t st);
+cudaError_t launch_count_floor(int measure, int dmax, const Thresh* thresh, u64* floor,
+                               cudaStream_t st);
 cudaError_t launch_scan_warp(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
 cudaError_t launch_scan_cta(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
 cudaError_t launch_scan_med(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);

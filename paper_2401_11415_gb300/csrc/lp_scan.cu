@@ -31,6 +31,7 @@
 //    and round(2^F / |Gamma_b|): integer addition is associative, so the
 //    sums do not depend on thread order.
 #include <float.h>
+#include <limits.h>
 #include <math.h>
 
 #include <algorithm>
@@ -45,6 +46,11 @@ namespace lp {
 __device__ __forceinline__ u32 hash_slot(int key, int logcap) {
   return ((u32)key * 0x9E3779B1u) >> (32 - logcap);
 }
+
+// Dense-window layout: counter i sits at position swz(i) (an involution that
+// keeps each aligned block of 32).  Hub lists step through the window with
+// near-constant strides; without it those strides fall on a few banks.
+__device__ __forceinline__ int swz(int i) { return i ^ ((i >> 5) & 31); }
 
 __host__ __device__ __forceinline__ int ceil_log2(u64 x) {
   int l = 0;
@@ -317,6 +323,33 @@ __device__ __forceinline__ int lower_bound_g(const int* __restrict__ idx, int l,
   return l;
 }
 
+// First index in idx[l, r) whose value is >= key.  The ids of an adjacency
+// list spread over the id range roughly evenly, so up to three interpolation
+// probes narrow the range before the bisection: fewer dependent loads than
+// bisection alone on long lists, and never more than three extra.
+__device__ __forceinline__ int lower_bound_interp(const int* __restrict__ idx, int l, int r,
+                                                  int key) {
+  if (l >= r) return l;
+  int vl = __ldg(idx + l);
+  if (vl >= key) return l;
+  int vr = __ldg(idx + r - 1);
+  if (vr < key) return r;
+  int lo = l, hi = r - 1;  // idx[lo] < key <= idx[hi]
+  for (int it = 0; it < 3 && hi - lo > 16; ++it) {
+    int g = lo + (int)(((long long)(key - vl) * (long long)(hi - lo)) / (long long)(vr - vl));
+    g = max(lo + 1, min(hi - 1, g));
+    const int v = __ldg(idx + g);
+    if (v < key) {
+      lo = g;
+      vl = v;
+    } else {
+      hi = g;
+      vr = v;
+    }
+  }
+  return lower_bound_g(idx, lo + 1, hi, key);
+}
+
 constexpr int kLongArc = 64;
 
 // The warp holds up to 32 arcs (lane j: suffix start s_j, length len_j,
@@ -565,6 +598,40 @@ __device__ __forceinline__ bool key_passes(const ScanArgs& A, const Thresh& T, i
   return pass;
 }
 
+// Global mode with a valid admission threshold T: the smallest count (or
+// fixed-point sum) v that can still reach T for a source of degree da.  Every
+// key grows with v, and for the measures that read |Gamma_c| the bound of
+// bound_below does too, so the counters below the floor are rejected by one
+// comparison.  Counts never exceed da (each counted intermediary is a
+// neighbour of the source); da + 1 means no counter can pass.
+__device__ __forceinline__ u64 count_floor(int measure, u64 da, const Thresh& T) {
+  if (!T.valid) return 1;
+  if (!needs_dc(measure)) return (T.num + T.den - 1) / T.den;  // key = v / 1
+  u64 lo = 1, hi = da + 1;
+  while (lo < hi) {
+    const u64 mid = (lo + hi) >> 1;
+    if (bound_below(measure, mid, da, T.num, T.den)) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// The floors of every source degree 0..dmax for the current threshold (one
+// thread per degree); rewritten whenever the threshold changes.
+__global__ void k_count_floor(int measure, int dmax, const Thresh* __restrict__ thresh,
+                              u64* __restrict__ floor) {
+  const Thresh T = *thresh;
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d <= dmax; d += gridDim.x * blockDim.x)
+    floor[d] = count_floor(measure, (u64)d, T);
+}
+
+cudaError_t launch_count_floor(int measure, int dmax, const Thresh* thresh, u64* floor,
+                               cudaStream_t st) {
+  const int threads = 256;
+  const int blocks = (int)std::min<long long>(((long long)dmax + threads) / threads, 4096);
+  k_count_floor<<<blocks, threads, 0, st>>>(measure, dmax, thresh, floor);
+  return cudaGetLastError();
+}
+
 // Score the live entries among four table slots per lane (value 0 = empty or
 // dead): the live ones are first gathered across the warp, then scored 32 at
 // a time with every lane busy.  Returns true if the global buffer
@@ -706,6 +773,7 @@ __device__ __forceinline__ bool score_hash_chunk(const ScanArgs& A, const Thresh
 
 // Score the touched counters of 32 bitmap words [w0, w0 + 32) of a dense
 // window (words at or beyond nwords are absent), clearing counters and bits.
+// Bit i marks the counter of vertex lg + i, held at position swz(i).
 // The set bits are first numbered across the warp (prefix sum of the word
 // popcounts), so every round scores 32 touched counters whatever their
 // spread over the words.
@@ -746,12 +814,79 @@ __device__ __forceinline__ bool score_dense_words(const ScanArgs& A, const Thres
     V v = 0;
     if (t < L) {
       const int i = (w0 + j) * 32 + nth_set_bit(wj, t - ej);
-      v = dense[i];
-      dense[i] = 0;
+      v = dense[swz(i)];
+      dense[swz(i)] = 0;
       c = lg + i;
       live = v != 0;  // 0: a first-order neighbour cleared by the exclusion
     }
     fail |= score_one<V, MODE>(A, T, a, da, live, c, v, top, tcnt, n_cand);
+  }
+  return fail;
+}
+
+// Global mode: score 128 consecutive dense counters per warp (positions
+// [base0, base0 + 128), four per lane) and clear them.  Position p holds the
+// counter of vertex lg + swz(p).  Counters below vmin are only counted.
+template <typename V>
+__device__ __forceinline__ bool score_dense_linear(const ScanArgs& A, const Thresh& T, int a,
+                                                   u64 da, V* dense, int base0, int npos, int lg,
+                                                   u64 vmin, u64& n_cand) {
+  const int base = base0 + lane_id() * 4;
+  V v4[4] = {0, 0, 0, 0};
+  if (base < npos) {
+    load4<V>(dense + base, v4);
+    if ((v4[0] | v4[1] | v4[2] | v4[3]) != 0) zero4<V>(dense + base);
+  }
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    n_cand += v4[j] != 0 ? 1 : 0;
+    any |= v4[j] != 0 && (u64)v4[j] >= vmin;
+  }
+  if (!__any_sync(FULLMASK, any)) return false;
+  bool fail = false;
+  u64 unused = 0;
+  int tcnt = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const bool live = v4[j] != 0 && (u64)v4[j] >= vmin;
+    fail |= score_one<V, 0>(A, T, a, da, live, lg + swz(base + j), v4[j], nullptr, tcnt, unused);
+  }
+  return fail;
+}
+
+// Global mode: score the 128-slot hash chunk [base0, base0 + 128) without
+// packing (most live slots fall below vmin) and clear it.
+template <typename V>
+__device__ __forceinline__ bool score_hash_linear(const ScanArgs& A, const Thresh& T, int a,
+                                                  u64 da, int* keys, V* vals, int base0, int nslots,
+                                                  u64 vmin, u64& n_cand) {
+  const int base = base0 + lane_id() * 4;
+  int4 k4 = make_int4(0, 0, 0, 0);
+  V v4[4] = {0, 0, 0, 0};
+  if (base < nslots) {
+    k4 = *reinterpret_cast<const int4*>(keys + base);
+    if ((k4.x | k4.y | k4.z | k4.w) != 0) {
+      load4<V>(vals + base, v4);
+      *reinterpret_cast<int4*>(keys + base) = make_int4(0, 0, 0, 0);
+      zero4<V>(vals + base);
+    }
+  }
+  const int kk[4] = {k4.x, k4.y, k4.z, k4.w};
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    n_cand += v4[j] != 0 ? 1 : 0;
+    any |= v4[j] != 0 && (u64)v4[j] >= vmin;
+  }
+  if (!__any_sync(FULLMASK, any)) return false;
+  bool fail = false;
+  u64 unused = 0;
+  int tcnt = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const bool live = v4[j] != 0 && (u64)v4[j] >= vmin;
+    fail |= score_one<V, 0>(A, T, a, da, live, kk[j] - 1, v4[j], nullptr, tcnt, unused);
   }
   return fail;
 }
@@ -1081,9 +1216,11 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 8)) k_scan_cta(
 
 // Shared memory of a large-tier CTA of THREADS threads beyond its table
 // (big_extra_smem(THREADS) bytes): a window-boundary table of
-// big_bounds(THREADS) positions, then a queue of THREADS long segments
-// (length / wedge prefix, start, weight).
-__host__ __device__ constexpr int big_bounds(int threads) { return 4 * threads; }
+// big_bounds(THREADS) positions, then a queue of THREADS segments (prefix,
+// start, length, weight): entries [0, THREADS / 2) hold segments of kPiece or
+// more wedges, cut into pieces of their own; entries [THREADS / 2, THREADS)
+// shorter ones, laid end to end and cut into pieces across segments.
+__host__ __device__ constexpr int big_bounds(int threads) { return 3 * threads; }
 constexpr int kPiece = 256;  // wedges per piece: eight per lane
 constexpr int kLongSeg = 64; // segments at least this long are shared as pieces
 constexpr int kShortSeg = 8; // the same when the item has at most one arc per thread
@@ -1172,18 +1309,21 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
   V* dense = reinterpret_cast<V*>(smem);
   u32* dbits = reinterpret_cast<u32*>(smem + (size_t)A.big_span * sizeof(V));  // touched bits
   int* bnd = reinterpret_cast<int*>(smem + table_bytes);  // boundaries or cursors
-  int* c_p = bnd + NB;                                    // queued segment: length, then prefix
-  int* c_s = c_p + THREADS;                               // start, then start - prefix
-  u64* c_w = reinterpret_cast<u64*>(c_s + THREADS);       // weight
+  int* c_p = bnd + NB;                                    // queued segment: prefix
+  int* c_s = c_p + THREADS;                               // start (short: start - prefix)
+  int* c_l = c_s + THREADS;                               // length
+  u64* c_w = reinterpret_cast<u64*>(c_l + THREADS);       // weight
   TopEnt* tops = reinterpret_cast<TopEnt*>(c_w + THREADS);
+  constexpr int H = THREADS / 2;                          // long entries [0, H), short [H, 2H)
   __shared__ int4 s_rec;
   __shared__ u64 s_next;
-  __shared__ int s_ndistinct, s_overflow, s_fail, s_qn;
+  __shared__ int s_ndistinct, s_overflow, s_fail, s_qnl, s_qns;
   __shared__ int s_tcnt[NW];
   __shared__ int2 s_wtot[NW];
   // optional phase profile (thread 0's clock): 0 item setup and boundary
-  // table, 1 segment bounds and prefix sum, 2 unused, 3 pieces, 4 exclusion
-  // and scoring, 5 item end
+  // table, 1 arc segments and short walks, 3 long-segment pieces, 4
+  // exclusion and scoring, 5 item end; 2 is the whole time of dense items
+  // (also counted in the others)
   long long t_prof[6] = {0, 0, 0, 0, 0, 0};
   long long t_last = clock64();
   const bool prof = A.prof != nullptr && threadIdx.x == 0;
@@ -1211,6 +1351,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
   for (;;) {
     const u64 qi = s_next;
     if (qi >= nq) break;
+    const long long t_item = prof ? clock64() : 0;
     if (threadIdx.x == 0) {
       s_rec = q[qi];
       s_fail = 0;
@@ -1244,11 +1385,12 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
         const Arc t = A.arc[e0 + j];
         const int s0 = MODE ? t.y - t.z : t.x + 1;
         const int key = lo + (int)(((u64)span * (u64)gg) / (u64)G);
-        bnd[q2] = (t.z <= A.cap && s0 < t.y) ? lower_bound_g(A.idx, s0, t.y, key) : s0;
+        bnd[q2] = (t.z <= A.cap && s0 < t.y) ? lower_bound_interp(A.idx, s0, t.y, key) : s0;
       }
       __syncthreads();
     }
     const u64 da = (u64)K;
+    const u64 vmin = MODE == 0 && T.valid ? __ldg(A.vfloor + K) : 1;
     TopEnt* top = tops + wid * (MODE ? A.k : 0);
     int tcnt = 0;
     bool fail = false;
@@ -1260,7 +1402,8 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
       if (threadIdx.x == 0) {
         s_ndistinct = 0;
         s_overflow = 0;
-        s_qn = 0;
+        s_qnl = 0;
+        s_qns = 0;
       }
       __syncthreads();
       LP_PHASE(0);
@@ -1268,9 +1411,14 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
         if (MODE == 1 && c == a) return;
         if (is_dense) {
           const int i = c - lg;
-          // the first add sees a zero low word (a later wrap to zero only
-          // sets the bit again)
-          if (shared_add<V>(&dense[i], wc) == 0) atomicOr(&dbits[i >> 5], 1u << (i & 31));
+          if (MODE == 0) {  // scored by a linear scan: no touched bits
+            if (sizeof(V) == 8) shared_add<V>(&dense[swz(i)], wc);
+            else atomicAdd(reinterpret_cast<u32*>(&dense[swz(i)]), (u32)wc);
+          } else if (shared_add<V>(&dense[swz(i)], wc) == 0) {
+            // the first add sees a zero low word (a later wrap to zero only
+            // sets the bit again)
+            atomicOr(&dbits[i >> 5], 1u << (i & 31));
+          }
         } else {
           if (*(volatile int*)&s_overflow) return;
           const int rc = hash_add<V>(keys, vals, logcap, c, wc);
@@ -1299,9 +1447,9 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
                 s0 = bnd[j * (G + 1) + g];
                 s1 = bnd[j * (G + 1) + g + 1];
               } else if (!full_range) {
-                const int b0 = (use_cur && g > 0) ? bnd[j] : lower_bound_g(A.idx, s0, s1, lg);
+                const int b0 = (use_cur && g > 0) ? bnd[j] : lower_bound_interp(A.idx, s0, s1, lg);
                 const int b1 = use_cur ? lower_bound_gallop(A.idx, b0, s1, hg)
-                                       : lower_bound_g(A.idx, b0, s1, hg);
+                                       : lower_bound_interp(A.idx, b0, s1, hg);
                 if (use_cur) bnd[j] = b1;
                 s0 = b0;
                 s1 = b1;
@@ -1312,12 +1460,14 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
             if (len > 0) w = arc_weight<V>(A, t.z);
           }
         }
-        if (len >= long_seg) {
-          const int slot = atomicAdd(&s_qn, 1);
-          if (slot < THREADS) {  // else the warp walks it below
-            c_s[slot] = st;
-            c_p[slot] = len;
-            c_w[slot] = (u64)w;
+        if (len >= long_seg) {  // queue it (a full queue: the warp walks it below)
+          const bool lng = len >= kPiece;
+          const int slot = atomicAdd(lng ? &s_qnl : &s_qns, 1);
+          if (slot < H) {
+            const int q2 = lng ? slot : H + slot;
+            c_s[q2] = st;
+            c_l[q2] = len;
+            c_w[q2] = (u64)w;
             len = 0;
           }
         }
@@ -1326,37 +1476,54 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
       }
       __syncthreads();
       LP_PHASE(1);
-      // phase B: the queued segments end to end, dealt to the warps in
-      // pieces of kPiece wedges
-      const int nqd = min(s_qn, THREADS);
-      if (nqd > 0 && (is_dense || !s_overflow)) {  // CTA-uniform
-        const int len = threadIdx.x < nqd ? c_p[threadIdx.x] : 0;
-        int ex, unused, tot, unused2;
-        block_scan2<THREADS>(len, 0, ex, unused, tot, unused2, s_wtot);
-        if (threadIdx.x < nqd) {
-          c_p[threadIdx.x] = ex;
-          c_s[threadIdx.x] -= ex;
+      // phase B: the queued segments in pieces of kPiece wedges dealt to the
+      // warps: the long ones piece by piece (one segment per piece, so a
+      // warp streams it), then the short ones end to end
+      const int nl = min(s_qnl, H), ns = min(s_qns, H);
+      if (nl + ns > 0 && (is_dense || !s_overflow)) {  // CTA-uniform
+        const int t = threadIdx.x;
+        const bool is_l = t < nl, is_s = t >= H && t < H + ns;
+        int ex, ey, npl, tsw;
+        block_scan2<THREADS>(is_l ? (c_l[t] + kPiece - 1) / kPiece : 0, is_s ? c_l[t] : 0, ex, ey,
+                             npl, tsw, s_wtot);
+        if (is_l) c_p[t] = ex;  // first piece of the segment
+        if (is_s) {             // first wedge of the segment in the concatenation
+          c_p[t] = ey;
+          c_s[t] -= ey;
         }
         __syncthreads();
-        for (int p = wid; p * kPiece < tot; p += NW) {  // warp-uniform trips
-          const int i0 = p * kPiece + lane;
-          int jj = i0 < tot ? last_le(c_p, 0, nqd, i0) : 0;
+        const int npieces = npl + (tsw + kPiece - 1) / kPiece;
+        for (int p = wid; p < npieces; p += NW) {  // warp-uniform trips
           int c8[8], j8[8];
+          if (p < npl) {
+            const int j = last_le(c_p, 0, nl, p);
+            const int off = (p - c_p[j]) * kPiece;
+            const int plen = min(kPiece, c_l[j] - off);
+            const int* src = A.idx + c_s[j] + off;
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int i = i0 + 32 * u;
-            c8[u] = -1;
-            if (i < tot) {
-              // i - 32 lay in segment jj and segments are not empty, so i
-              // lies in one of the segments jj .. jj + 32
-              if (jj + 1 < nqd && c_p[jj + 1] <= i) jj = last_le(c_p, jj + 1, min(nqd, jj + 33), i);
-              c8[u] = __ldg(A.idx + c_s[jj] + i);
+            for (int u = 0; u < 8; ++u) {
+              c8[u] = lane + 32 * u < plen ? __ldg(src + lane + 32 * u) : -1;
+              j8[u] = j;
+            }
+          } else {
+            const int i0 = (p - npl) * kPiece + lane;
+            int jj = i0 < tsw ? last_le(c_p, H, H + ns, i0) : H;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int i = i0 + 32 * u;
+              c8[u] = -1;
+              if (i < tsw) {
+                // i - 32 lay in segment jj and segments are not empty, so i
+                // lies in one of the segments jj .. jj + 32
+                if (jj + 1 < H + ns && c_p[jj + 1] <= i) jj = last_le(c_p, jj + 1, min(H + ns, jj + 33), i);
+                c8[u] = __ldg(A.idx + c_s[jj] + i);
+              }
               j8[u] = jj;
             }
           }
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            if (c8[u] >= 0) insert(c8[u], (V)c_w[j8[u]]);
+            if (c8[u] >= 0) insert(c8[u], V64 ? (V)c_w[j8[u]] : (V)1);
           if (!is_dense && __any_sync(FULLMASK, *(volatile int*)&s_overflow != 0)) break;
         }
         __syncthreads();
@@ -1376,12 +1543,21 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
       for (int e = e0 + threadIdx.x; e < e1; e += THREADS) {
         const int b = __ldg(A.idx + e);
         if (b < lg || b >= hg || (MODE == 0 && b <= a)) continue;
-        if (is_dense) dense[b - lg] = 0;
+        if (is_dense) dense[swz(b - lg)] = 0;
         else hash_kill<V>(keys, vals, logcap, b);
       }
       __syncthreads();
-      // score and select: touched counters (dense) or packed live slots (hash)
-      if (is_dense) {
+      // score and select.  Global mode: every counter or slot once, the ones
+      // below the count floor only counted.  Per-source mode: the touched
+      // counters (dense) or the packed live slots (hash).
+      if (MODE == 0 && is_dense) {
+        const int npos = (hg - lg + 31) & ~31;
+        for (int base0 = wid * 128; base0 < npos; base0 += THREADS * 4)  // warp-uniform trips
+          fail |= score_dense_linear<V>(A, T, a, da, dense, base0, npos, lg, vmin, n_cand);
+      } else if (MODE == 0 && T.valid) {
+        for (int base0 = wid * 128; base0 < nslots; base0 += THREADS * 4)
+          fail |= score_hash_linear<V>(A, T, a, da, keys, vals, base0, nslots, vmin, n_cand);
+      } else if (is_dense) {
         const int nwords = (hg - lg + 31) >> 5;
         for (int w0 = wid * 32; w0 < nwords; w0 += THREADS)  // warp-uniform trips
           fail |= score_dense_words<V, MODE>(A, T, a, da, dense, dbits, w0, nwords, lg, top, tcnt,
@@ -1444,6 +1620,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
     }
     __syncthreads();
     LP_PHASE(5);
+    if (prof && is_dense) t_prof[2] += clock64() - t_item;
   }
 #undef LP_PHASE
   if (prof)
@@ -1567,41 +1744,55 @@ __global__ void k_pair_cn(lp_link* __restrict__ links, const int* __restrict__ c
   const int dy = ye - ys;
   const int dx = xe - xs;
   int c = 0;
-  if (dx <= 64 || dy > 16 * dx || cap <= 4096) {
-    // short Gamma_x or a much longer Gamma_y: look each b of Gamma_x up
+  if (dx <= 64 || dy > 16 * dx || cap < 256) {
+    // short Gamma_x, a much longer Gamma_y or a low hub limit (most b are
+    // skipped without a search): look each b of Gamma_x up
     for (int e = xs + lane; e < xe; e += 32) {
       const Arc t = arc[e];  // b = t.w, |Gamma_b| = t.z, Gamma_b ends at t.y
       const int b = t.w, db = t.z;
       if (db > cap) continue;
       if (db <= dy) {
         const int be = t.y, bs = be - db;
-        const int p = lower_bound_g(idx, bs, be, y);
+        const int p = lower_bound_interp(idx, bs, be, y);
         c += (p < be && __ldg(idx + p) == y) ? 1 : 0;
       } else {
-        const int p = lower_bound_g(idx, ys, ye, b);
+        const int p = lower_bound_interp(idx, ys, ye, b);
         c += (p < ye && __ldg(idx + p) == b) ? 1 : 0;
       }
     }
   } else {
-    // comparable long lists: merge path, each lane merges 1/32 of the
-    // combined length; a match at a lane boundary is counted by the lane
-    // that holds its Gamma_x element (Gamma_x first on ties)
-    const int tot = dx + dy;
-    auto split = [&](int d) {  // elements of Gamma_x among the first d merged
-      int lo = d > dy ? d - dy : 0, hi = d < dx ? d : dx;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(idx + xs + mid) <= __ldg(idx + ys + d - 1 - mid)) lo = mid + 1; else hi = mid;
+    // comparable long lists: both walked in 32-element tiles, one element
+    // per lane.  Each lane looks its Gamma_x element up in the current Gamma_y
+    // tile (binary search over the lanes); then the tile with the smaller last
+    // element moves on (both on a tie), with the next tiles already loading.
+    // A common element is in both tiles during exactly one step.
+    const int* X = idx + xs;
+    const int* Y = idx + ys;
+    int i = 0, j = 0;
+    int xv = lane < dx ? __ldg(X + lane) : INT_MAX;
+    int yv = lane < dy ? __ldg(Y + lane) : INT_MAX;
+    int xn = 32 + lane < dx ? __ldg(X + 32 + lane) : INT_MAX;
+    int yn = 32 + lane < dy ? __ldg(Y + 32 + lane) : INT_MAX;
+    while (i < dx && j < dy) {  // warp-uniform
+      int p = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1)
+        if (__shfl_sync(FULLMASK, yv, p + step - 1) < xv) p += step;
+      const int yp = __shfl_sync(FULLMASK, yv, p);  // every lane takes part
+      bool hit = xv != INT_MAX && yp == xv;
+      if (hit && cap < INT_MAX) hit = __ldg(deg + xv) <= cap;
+      c += hit ? 1 : 0;
+      const int lx = __shfl_sync(FULLMASK, xv, 31), ly = __shfl_sync(FULLMASK, yv, 31);
+      if (lx <= ly) {
+        i += 32;
+        xv = xn;
+        xn = i + 32 + lane < dx ? __ldg(X + i + 32 + lane) : INT_MAX;
       }
-      return lo;
-    };
-    const int d0 = (int)(((long long)tot * lane) / 32), d1 = (int)(((long long)tot * (lane + 1)) / 32);
-    const int i0 = split(d0), i1 = split(d1);
-    int j = d0 - i0;
-    for (int i = i0; i < i1; ++i) {
-      const int xi = __ldg(idx + xs + i);
-      while (j < dy && __ldg(idx + ys + j) < xi) ++j;
-      if (j < dy && __ldg(idx + ys + j) == xi && __ldg(deg + xi) <= cap) ++c;
+      if (ly <= lx) {
+        j += 32;
+        yv = yn;
+        yn = j + 32 + lane < dy ? __ldg(Y + j + 32 + lane) : INT_MAX;
+      }
     }
   }
   c = __reduce_add_sync(FULLMASK, (u32)c);
@@ -1699,7 +1890,7 @@ static cudaError_t launch_cta_t(const ScanArgs& A, const int4* q, u64 nq, int ta
 
 template <bool V64, int MODE, int THREADS>
 static cudaError_t launch_big_t(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st) {
-  static_assert(big_extra_smem(THREADS) == big_bounds(THREADS) * 4 + THREADS * (4 + 4 + 8),
+  static_assert(big_extra_smem(THREADS) == big_bounds(THREADS) * 4 + THREADS * (4 + 4 + 4 + 8),
                 "large-tier shared memory layout");
   const int tb = A.big_bytes;
   const size_t smem = (size_t)tb + big_extra_smem(THREADS) +
