@@ -388,19 +388,18 @@ struct Queues {
 };
 
 // Launch the scan kernels; with timing on, time each on the graph's stream.
-// Launch the scan of the tiers in `tiers` (bit t: tier t), smallest sources
-// first: in the global mode their candidates are the first to reach the
-// selection buffer, and they tend to rank high (few neighbours, high overlap).
+// Launch the scan of every tier, smallest sources first; of the large tier
+// only the first large_limit items (the rest stay queued).
 static cudaError_t scan_launches(Graph& g, const ScanArgs& A, const Queues& Q, bool timing,
-                                 int tiers = 7) {
+                                 u64 large_limit = ~0ull) {
   cudaStream_t st = g.stream;
   for (int t = 0; t < 3; ++t) {
-    if (!Q.n[t] || !(tiers & (1 << t))) continue;
+    const u64 n = t == 2 ? std::min(Q.n[t], large_limit) : Q.n[t];
+    if (!n) continue;
     if (timing) cudaEventRecord(g.kev[2 * t], st);
     const int4* q = sp<int4>(*Q.cur[t]);
-    cudaError_t e = t == 0 ? launch_scan_warp(A, q, Q.n[t], st)
-                           : (t == 1 ? launch_scan_med(A, q, Q.n[t], st)
-                                     : launch_scan_cta(A, q, Q.n[t], st));
+    cudaError_t e = t == 0 ? launch_scan_warp(A, q, n, st)
+                           : (t == 1 ? launch_scan_med(A, q, n, st) : launch_scan_cta(A, q, n, st));
     if (e != cudaSuccess) return e;
     if (timing) cudaEventRecord(g.kev[2 * t + 1], st);
     t_stats.tier_launches[t]++;
@@ -410,12 +409,11 @@ static cudaError_t scan_launches(Graph& g, const ScanArgs& A, const Queues& Q, b
 }
 
 // After the stream synchronised: add the kernels' event times to the stats.
-static void scan_times(Graph& g, const Queues& Q, bool timing, int tiers = 7) {
+static void scan_times(Graph& g, const Queues& Q, bool timing) {
   if (!timing) return;
   for (int t = 0; t < 3; ++t) {
     float ms = 0.f;
-    if (Q.n[t] && (tiers & (1 << t)) &&
-        cudaEventElapsedTime(&ms, g.kev[2 * t], g.kev[2 * t + 1]) == cudaSuccess)
+    if (Q.n[t] && cudaEventElapsedTime(&ms, g.kev[2 * t], g.kev[2 * t + 1]) == cudaSuccess)
       t_stats.tier_ms[t] += ms;
   }
 }
@@ -662,13 +660,15 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
     A.split = sp<int4>(g.s_split);
     A.split_cap = split_cap;
     A.prof = options_snapshot().phase_profile ? d_ctr->prof : nullptr;
-    // first round: the warp and medium tiers alone, so that the threshold
-    // they set (a compaction below) already filters the large tier
-    const bool seed = round == 0 && k > 0 && Q.n[2] > 0 && Q.n[0] + Q.n[1] > 0;
-    CU(scan_launches(g, A, Q, tm.on, seed ? 3 : 7));
+    // first round: the small tiers and an eighth of the large tier (items
+    // in source order, a sample of the sources), so that the threshold they
+    // set (a compaction below) already filters the rest of the large tier
+    const bool seed = round == 0 && k > 0 && Q.n[2] >= 64;
+    const u64 large_n = seed ? Q.n[2] / 8 : Q.n[2];
+    CU(scan_launches(g, A, Q, tm.on, large_n));
     CU(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    scan_times(g, Q, tm.on, seed ? 3 : 7);
+    scan_times(g, Q, tm.on);
     for (int i = 0; i < 6; ++i) t_stats.phase_cycles[i] += (int64_t)h.prof[i];
     if (h.error) return fail(LP_EINTERNAL, "lp_predict: device check %u", h.error);
     t_stats.candidates += (int64_t)h.candidates;
@@ -679,7 +679,7 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
     if (h.nsplit)
       CU(cudaMemcpy(splits.data(), g.s_split.p, sizeof(int4) * h.nsplit, cudaMemcpyDeviceToHost));
     const u64 done[3] = {std::min<u64>(h.claim_w, Q.n[0]), std::min<u64>(h.claim_m, Q.n[1]),
-                         std::min<u64>(h.claim_c, Q.n[2])};
+                         std::min<u64>(h.claim_c, large_n)};
     const u64 valid = std::min<u64>(h.cand_cnt, C);
     t_stats.splits += (int32_t)h.nsplit;
     if (h.full || (seed && valid >= (u64)k)) {
