@@ -583,14 +583,14 @@ __device__ __forceinline__ bool bound_below(int measure, u64 v, u64 da, u64 tn, 
 template <typename V, int MODE>
 __device__ __forceinline__ bool key_passes(const ScanArgs& A, const Thresh& T, int a, u64 da,
                                            int c, V v, const TopEnt* top, int tcnt, u64& num,
-                                           u64& den) {
+                                           u64& den, int dc_in = -1) {
   u64 dc = 0;
   if (needs_dc(A.measure)) {
     if (MODE == 0 && T.valid && bound_below(A.measure, (u64)v, da, T.num, T.den)) return false;
     if (MODE == 1 && tcnt >= A.k &&
         bound_below(A.measure, (u64)v, da, top[A.k - 1].num, top[A.k - 1].den))
       return false;
-    dc = (u64)__ldg(A.deg + c);
+    dc = dc_in >= 0 ? (u64)dc_in : (u64)__ldg(A.deg + c);
   }
   make_key(A.measure, (u64)v, da, dc, num, den);
   bool pass = !A.thr_check || key_value(A.measure, num, den, (u64)v, A.fixbits) > A.threshold;
@@ -693,12 +693,12 @@ __device__ __forceinline__ bool score_chunk(const ScanArgs& A, const Thresh& T, 
 template <typename V, int MODE>
 __device__ __forceinline__ bool score_one(const ScanArgs& A, const Thresh& T, int a, u64 da,
                                           bool live, int c, V v, TopEnt* top, int& tcnt,
-                                          u64& n_cand) {
+                                          u64& n_cand, int dc_in = -1) {
   u64 num = 0, den = 1;
   bool pass = false;
   if (live) {
     ++n_cand;
-    pass = key_passes<V, MODE>(A, T, a, da, c, v, top, tcnt, num, den);
+    pass = key_passes<V, MODE>(A, T, a, da, c, v, top, tcnt, num, den, dc_in);
   }
   if (MODE == 0) return admit_global(A, pass, num, den, a, c);
   TopEnt x;
@@ -824,43 +824,76 @@ __device__ __forceinline__ bool score_dense_words(const ScanArgs& A, const Thres
   return fail;
 }
 
-// Global mode: score 128 consecutive dense counters per warp (positions
-// [base0, base0 + 128), four per lane) and clear them.  Position p holds the
-// counter of vertex lg + swz(p).  Counters below vmin are only counted.
+// Global mode, large tier: counters at or above the count floor ("survivors")
+// still need the exact test, most of them |Gamma_c| too.  Each warp queues
+// them in registers (lane i holds entry i; qn entries, warp-uniform), the
+// degree load issued as the entry is queued, and tests 32 at a time, so the
+// loads overlap the scan instead of stalling it.
+template <typename V>
+__device__ __forceinline__ bool survivors_flush(const ScanArgs& A, const Thresh& T, int a, u64 da,
+                                                int& qn, int qc, V qv, int qd) {
+  u64 unused = 0;
+  int tcnt = 0;
+  const bool fail =
+      score_one<V, 0>(A, T, a, da, lane_id() < qn, qc, qv, nullptr, tcnt, unused, qd);
+  qn = 0;
+  return fail;
+}
+
+template <typename V>
+__device__ __forceinline__ bool survivors_push(const ScanArgs& A, const Thresh& T, int a, u64 da,
+                                               bool live, int c, V v, int& qn, int& qc, V& qv,
+                                               int& qd) {
+  const u32 m = __ballot_sync(FULLMASK, live);
+  if (m == 0) return false;
+  const int k = __popc(m);
+  bool fail = false;
+  if (qn + k > 32) fail = survivors_flush<V>(A, T, a, da, qn, qc, qv, qd);
+  const int t = lane_id() - qn;  // this lane receives new entry t
+  const bool recv = t >= 0 && t < k;
+  const int src = recv ? nth_set_bit(m, t) : lane_id();
+  const int nc = __shfl_sync(FULLMASK, c, src);
+  const V nv = __shfl_sync(FULLMASK, v, src);
+  if (recv) {
+    qc = nc;
+    qv = nv;
+    qd = needs_dc(A.measure) ? __ldg(A.deg + nc) : 0;
+  }
+  qn += k;
+  return fail;
+}
+
+// Global mode: 128 consecutive dense counters per warp (positions [base0,
+// base0 + 128), four per lane), cleared; the ones at or above vmin are queued.
+// Position p holds the counter of vertex lg + swz(p).
 template <typename V>
 __device__ __forceinline__ bool score_dense_linear(const ScanArgs& A, const Thresh& T, int a,
                                                    u64 da, V* dense, int base0, int npos, int lg,
-                                                   u64 vmin, u64& n_cand) {
+                                                   u64 vmin, u64& n_cand, int& qn, int& qc,
+                                                   V& qv, int& qd) {
   const int base = base0 + lane_id() * 4;
   V v4[4] = {0, 0, 0, 0};
   if (base < npos) {
     load4<V>(dense + base, v4);
     if ((v4[0] | v4[1] | v4[2] | v4[3]) != 0) zero4<V>(dense + base);
   }
-  bool any = false;
+  bool fail = false;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     n_cand += v4[j] != 0 ? 1 : 0;
-    any |= v4[j] != 0 && (u64)v4[j] >= vmin;
-  }
-  if (!__any_sync(FULLMASK, any)) return false;
-  bool fail = false;
-  u64 unused = 0;
-  int tcnt = 0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
     const bool live = v4[j] != 0 && (u64)v4[j] >= vmin;
-    fail |= score_one<V, 0>(A, T, a, da, live, lg + swz(base + j), v4[j], nullptr, tcnt, unused);
+    fail |= survivors_push<V>(A, T, a, da, live, lg + swz(base + j), v4[j], qn, qc, qv, qd);
   }
   return fail;
 }
 
-// Global mode: score the 128-slot hash chunk [base0, base0 + 128) without
-// packing (most live slots fall below vmin) and clear it.
+// Global mode: the 128-slot hash chunk [base0, base0 + 128), cleared; the
+// live slots at or above vmin are queued.
 template <typename V>
 __device__ __forceinline__ bool score_hash_linear(const ScanArgs& A, const Thresh& T, int a,
                                                   u64 da, int* keys, V* vals, int base0, int nslots,
-                                                  u64 vmin, u64& n_cand) {
+                                                  u64 vmin, u64& n_cand, int& qn, int& qc, V& qv,
+                                                  int& qd) {
   const int base = base0 + lane_id() * 4;
   int4 k4 = make_int4(0, 0, 0, 0);
   V v4[4] = {0, 0, 0, 0};
@@ -873,20 +906,12 @@ __device__ __forceinline__ bool score_hash_linear(const ScanArgs& A, const Thres
     }
   }
   const int kk[4] = {k4.x, k4.y, k4.z, k4.w};
-  bool any = false;
+  bool fail = false;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     n_cand += v4[j] != 0 ? 1 : 0;
-    any |= v4[j] != 0 && (u64)v4[j] >= vmin;
-  }
-  if (!__any_sync(FULLMASK, any)) return false;
-  bool fail = false;
-  u64 unused = 0;
-  int tcnt = 0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
     const bool live = v4[j] != 0 && (u64)v4[j] >= vmin;
-    fail |= score_one<V, 0>(A, T, a, da, live, kk[j] - 1, v4[j], nullptr, tcnt, unused);
+    fail |= survivors_push<V>(A, T, a, da, live, kk[j] - 1, v4[j], qn, qc, qv, qd);
   }
   return fail;
 }
@@ -1221,7 +1246,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 8)) k_scan_cta(
 // more wedges, cut into pieces of their own; entries [THREADS / 2, THREADS)
 // shorter ones, laid end to end and cut into pieces across segments.
 __host__ __device__ constexpr int big_bounds(int threads) { return 3 * threads; }
-constexpr int kPiece = 256;  // wedges per piece: eight per lane
+constexpr int kPiece = 128;  // wedges per piece
+constexpr int kPerLane = kPiece / 32;
 constexpr int kLongSeg = 64; // segments at least this long are shared as pieces
 constexpr int kShortSeg = 8; // the same when the item has at most one arc per thread
 
@@ -1494,14 +1520,14 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
         __syncthreads();
         const int npieces = npl + (tsw + kPiece - 1) / kPiece;
         for (int p = wid; p < npieces; p += NW) {  // warp-uniform trips
-          int c8[8], j8[8];
+          int c8[kPerLane], j8[kPerLane];
           if (p < npl) {
             const int j = last_le(c_p, 0, nl, p);
             const int off = (p - c_p[j]) * kPiece;
             const int plen = min(kPiece, c_l[j] - off);
             const int* src = A.idx + c_s[j] + off;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < kPerLane; ++u) {
               c8[u] = lane + 32 * u < plen ? __ldg(src + lane + 32 * u) : -1;
               j8[u] = j;
             }
@@ -1509,7 +1535,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
             const int i0 = (p - npl) * kPiece + lane;
             int jj = i0 < tsw ? last_le(c_p, H, H + ns, i0) : H;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < kPerLane; ++u) {
               const int i = i0 + 32 * u;
               c8[u] = -1;
               if (i < tsw) {
@@ -1522,7 +1548,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
             }
           }
 #pragma unroll
-          for (int u = 0; u < 8; ++u)
+          for (int u = 0; u < kPerLane; ++u)
             if (c8[u] >= 0) insert(c8[u], V64 ? (V)c_w[j8[u]] : (V)1);
           if (!is_dense && __any_sync(FULLMASK, *(volatile int*)&s_overflow != 0)) break;
         }
@@ -1550,13 +1576,20 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
       // score and select.  Global mode: every counter or slot once, the ones
       // below the count floor only counted.  Per-source mode: the touched
       // counters (dense) or the packed live slots (hash).
-      if (MODE == 0 && is_dense) {
-        const int npos = (hg - lg + 31) & ~31;
-        for (int base0 = wid * 128; base0 < npos; base0 += THREADS * 4)  // warp-uniform trips
-          fail |= score_dense_linear<V>(A, T, a, da, dense, base0, npos, lg, vmin, n_cand);
-      } else if (MODE == 0 && T.valid) {
-        for (int base0 = wid * 128; base0 < nslots; base0 += THREADS * 4)
-          fail |= score_hash_linear<V>(A, T, a, da, keys, vals, base0, nslots, vmin, n_cand);
+      if (MODE == 0 && (is_dense || T.valid)) {
+        int qn = 0, qc = 0, qd = 0;
+        V qv = 0;
+        if (is_dense) {
+          const int npos = (hg - lg + 31) & ~31;
+          for (int base0 = wid * 128; base0 < npos; base0 += THREADS * 4)  // warp-uniform trips
+            fail |= score_dense_linear<V>(A, T, a, da, dense, base0, npos, lg, vmin, n_cand, qn,
+                                          qc, qv, qd);
+        } else {
+          for (int base0 = wid * 128; base0 < nslots; base0 += THREADS * 4)
+            fail |= score_hash_linear<V>(A, T, a, da, keys, vals, base0, nslots, vmin, n_cand, qn,
+                                         qc, qv, qd);
+        }
+        if (qn > 0) fail |= survivors_flush<V>(A, T, a, da, qn, qc, qv, qd);
       } else if (is_dense) {
         const int nwords = (hg - lg + 31) >> 5;
         for (int w0 = wid * 32; w0 < nwords; w0 += THREADS)  // warp-uniform trips
