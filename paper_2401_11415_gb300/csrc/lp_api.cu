@@ -455,8 +455,12 @@ static ScanArgs base_args(Graph& g, int measure, int cap, double threshold, int 
   A.big_bytes = big_bytes;
   A.big_logcap = big_logcap;
   // dense window (128-aligned): in the global mode counters only (scored by
-  // a linear scan), in the per-source mode counters plus one touched bit each
-  A.big_span = mode == 0 ? (int)(((long long)big_bytes / vbytes) & ~127ll)
+  // a linear scan; 16-bit for the count measures while every count, at most
+  // the source degree, stays below 2^16), in the per-source mode counters
+  // plus one touched bit each
+  A.dense16 = mode == 0 && !v64 && g.dmax < 65536;
+  const int cbytes = A.dense16 ? 2 : vbytes;
+  A.big_span = mode == 0 ? (int)(((long long)big_bytes / cbytes) & ~127ll)
                          : (int)(((long long)big_bytes * 8 / (8 * vbytes + 1)) & ~127ll);
   A.warp_max = std::min(o.warp_max, kWarpMaxWedges);
   A.med_max = std::max(A.warp_max, std::min(o.med_max, kMedMaxWedges));

@@ -877,12 +877,50 @@ __device__ __forceinline__ bool score_dense_linear(const ScanArgs& A, const Thre
     load4<V>(dense + base, v4);
     if ((v4[0] | v4[1] | v4[2] | v4[3]) != 0) zero4<V>(dense + base);
   }
-  bool fail = false;
+  bool any = false;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     n_cand += v4[j] != 0 ? 1 : 0;
+    any |= v4[j] != 0 && (u64)v4[j] >= vmin;
+  }
+  if (!__any_sync(FULLMASK, any)) return false;
+  bool fail = false;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
     const bool live = v4[j] != 0 && (u64)v4[j] >= vmin;
     fail |= survivors_push<V>(A, T, a, da, live, lg + swz(base + j), v4[j], qn, qc, qv, qd);
+  }
+  return fail;
+}
+
+// The same for 16-bit counters, two per word (count measures, counts below
+// 2^16): 256 positions per warp, eight per lane.
+__device__ __forceinline__ bool score_dense16_linear(const ScanArgs& A, const Thresh& T, int a,
+                                                     u64 da, u32* words, int base0, int npos,
+                                                     int lg, u64 vmin, u64& n_cand, int& qn,
+                                                     int& qc, u32& qv, int& qd) {
+  const int base = base0 + lane_id() * 8;
+  uint4 w = make_uint4(0, 0, 0, 0);
+  if (base < npos) {
+    w = *reinterpret_cast<const uint4*>(words + (base >> 1));
+    if ((w.x | w.y | w.z | w.w) != 0)
+      *reinterpret_cast<uint4*>(words + (base >> 1)) = make_uint4(0, 0, 0, 0);
+  }
+  const u32 ww[4] = {w.x, w.y, w.z, w.w};
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const u32 v = (ww[j >> 1] >> ((j & 1) << 4)) & 0xffffu;
+    n_cand += v != 0 ? 1 : 0;
+    any |= v != 0 && (u64)v >= vmin;
+  }
+  if (!__any_sync(FULLMASK, any)) return false;
+  bool fail = false;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const u32 v = (ww[j >> 1] >> ((j & 1) << 4)) & 0xffffu;
+    const bool live = v != 0 && (u64)v >= vmin;
+    fail |= survivors_push<u32>(A, T, a, da, live, lg + swz(base + j), v, qn, qc, qv, qd);
   }
   return fail;
 }
@@ -906,10 +944,16 @@ __device__ __forceinline__ bool score_hash_linear(const ScanArgs& A, const Thres
     }
   }
   const int kk[4] = {k4.x, k4.y, k4.z, k4.w};
-  bool fail = false;
+  bool any = false;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     n_cand += v4[j] != 0 ? 1 : 0;
+    any |= v4[j] != 0 && (u64)v4[j] >= vmin;
+  }
+  if (!__any_sync(FULLMASK, any)) return false;
+  bool fail = false;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
     const bool live = v4[j] != 0 && (u64)v4[j] >= vmin;
     fail |= survivors_push<V>(A, T, a, da, live, kk[j] - 1, v4[j], qn, qc, qv, qd);
   }
@@ -1364,6 +1408,8 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
 
   const int lane = lane_id();
   const int wid = threadIdx.x >> 5;
+  // global mode, count measures: dense windows of 16-bit counters
+  const bool d16 = MODE == 0 && !V64 && A.dense16;
   for (int i = threadIdx.x * 16; i < table_bytes; i += THREADS * 16)
     *reinterpret_cast<int4*>(smem + i) = make_int4(0, 0, 0, 0);
   Thresh T;
@@ -1438,8 +1484,14 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
         if (is_dense) {
           const int i = c - lg;
           if (MODE == 0) {  // scored by a linear scan: no touched bits
-            if (sizeof(V) == 8) shared_add<V>(&dense[swz(i)], wc);
-            else atomicAdd(reinterpret_cast<u32*>(&dense[swz(i)]), (u32)wc);
+            if (sizeof(V) == 8) {
+              shared_add<V>(&dense[swz(i)], wc);
+            } else if (d16) {  // count measures: the weight is 1
+              const int p = swz(i);
+              atomicAdd(reinterpret_cast<u32*>(dense) + (p >> 1), 1u << ((p & 1) << 4));
+            } else {
+              atomicAdd(reinterpret_cast<u32*>(&dense[swz(i)]), (u32)wc);
+            }
           } else if (shared_add<V>(&dense[swz(i)], wc) == 0) {
             // the first add sees a zero low word (a later wrap to zero only
             // sets the bit again)
@@ -1569,7 +1621,12 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
       for (int e = e0 + threadIdx.x; e < e1; e += THREADS) {
         const int b = __ldg(A.idx + e);
         if (b < lg || b >= hg || (MODE == 0 && b <= a)) continue;
-        if (is_dense) dense[swz(b - lg)] = 0;
+        if (is_dense && d16) {
+          const int p = swz(b - lg);
+          atomicAnd(reinterpret_cast<u32*>(dense) + (p >> 1), ~(0xffffu << ((p & 1) << 4)));
+        } else if (is_dense) {
+          dense[swz(b - lg)] = 0;
+        }
         else hash_kill<V>(keys, vals, logcap, b);
       }
       __syncthreads();
@@ -1579,7 +1636,14 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
       if (MODE == 0 && (is_dense || T.valid)) {
         int qn = 0, qc = 0, qd = 0;
         V qv = 0;
-        if (is_dense) {
+        if (is_dense && d16) {
+          const int npos = (hg - lg + 31) & ~31;
+          u32 qv16 = (u32)qv;
+          for (int base0 = wid * 256; base0 < npos; base0 += THREADS * 8)  // warp-uniform trips
+            fail |= score_dense16_linear(A, T, a, da, reinterpret_cast<u32*>(dense), base0, npos,
+                                         lg, vmin, n_cand, qn, qc, qv16, qd);
+          qv = (V)qv16;
+        } else if (is_dense) {
           const int npos = (hg - lg + 31) & ~31;
           for (int base0 = wid * 128; base0 < npos; base0 += THREADS * 4)  // warp-uniform trips
             fail |= score_dense_linear<V>(A, T, a, da, dense, base0, npos, lg, vmin, n_cand, qn,
