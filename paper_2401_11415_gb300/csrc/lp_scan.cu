@@ -1507,13 +1507,14 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
           }
         }
       };
-      // phase A: each warp takes 32 arcs at a time, one per lane; short
-      // segments are walked at once (concatenated across the lanes), longer
-      // ones are queued for phase B.  With fewer arcs than threads most warps
-      // hold no arc, so all but the shortest segments are queued.
+      // phase A: one arc per thread, THREADS arcs at a time, dealt round-robin
+      // to the warps (arc eb + lane * NW + wid) so that a source with few arcs
+      // still spreads them over every warp; short segments are walked at once
+      // (concatenated across the lanes), longer ones are queued for phase B.
+      // With at most one arc per thread all but the shortest are queued.
       const int long_seg = K <= THREADS ? kShortSeg : kLongSeg;
-      for (int eb = wid * 32; eb < K; eb += NW * 32) {  // warp-uniform trips
-        const int j = eb + lane;
+      for (int eb = 0; eb < K; eb += THREADS) {  // CTA-uniform trips
+        const int j = eb + lane * NW + wid;
         int st = 0, len = 0;
         V w = 0;
         if (j < K) {
