@@ -129,7 +129,8 @@ static void free_graph(Graph* g) {
   Graph::Scratch* all[] = {&g->s_ctr, &g->s_w, &g->s_warpq, &g->s_itemq, &g->s_warpq2,
                            &g->s_itemq2, &g->s_medq, &g->s_medq2, &g->s_buf, &g->s_buf2,
                            &g->s_buf3, &g->s_misc, &g->s_failed, &g->s_split,
-                           &g->s_thresh, &g->s_vfloor, &g->s_flags, &g->s_partial, &g->s_phdr, &g->s_top,
+                           &g->s_thresh, &g->s_vfloor, &g->s_pair, &g->s_flags, &g->s_partial,
+                           &g->s_phdr, &g->s_top,
                            &g->s_cnt, &g->s_links, &g->s_src, &g->s_grp};
   for (auto* s : all)
     if (s->p) cudaFree(s->p);
@@ -771,8 +772,17 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
     CU(launch_emit_global(res, nwrite, measure, g.fixbits, d_links, st));
     t_stats.launches++;
     if (measure == LP_AA || measure == LP_RA) {
-      CU(launch_pair_cn(d_links, nullptr, 1, nwrite, g.d_off, g.d_idx, g.d_deg, g.d_arc, A.cap, st));
-      t_stats.launches++;
+      // grouped by u when hubs take part (their lists are long and shared by
+      // many links); with a low hub limit the per-link lookups skip most b
+      if (A.cap >= 256 && pair_groups_fit(g.n)) {
+        CU(ensure(g, g.s_pair, pair_groups_scratch(g.n, nwrite)));
+        CU(launch_pair_cn_groups(d_links, nwrite, g.n, g.d_off, g.d_idx, g.d_arc, A.cap,
+                                 g.s_pair.p, st, &t_stats.launches));
+      } else {
+        CU(launch_pair_cn(d_links, nullptr, 1, nwrite, g.d_off, g.d_idx, g.d_deg, g.d_arc, A.cap,
+                          st));
+        t_stats.launches++;
+      }
     }
     if (!out_dev)
       CU(cudaMemcpyAsync(out, d_links, sizeof(lp_link) * nwrite, cudaMemcpyDeviceToHost, st));

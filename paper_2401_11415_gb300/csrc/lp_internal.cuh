@@ -174,7 +174,7 @@ struct Graph {
   };
   Scratch s_ctr, s_w, s_warpq, s_itemq, s_warpq2, s_itemq2, s_medq, s_medq2, s_buf, s_buf2,
       s_failed, s_split, s_thresh, s_flags, s_partial, s_phdr, s_top, s_cnt, s_links, s_src, s_grp,
-      s_buf3, s_misc, s_vfloor;
+      s_buf3, s_misc, s_vfloor, s_pair;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // per kernel
 };
@@ -221,6 +221,14 @@ cudaError_t launch_emit_global(const Cand* c, u64 n, int measure, int fixbits, l
                                cudaStream_t st);
 cudaError_t launch_emit_sources(const TopEnt* top, const int* cnt, const int* sources, int n_src,
                                 int k, int measure, int fixbits, lp_link* out, cudaStream_t st);
+// Common-neighbour counts of global-mode links grouped by u (lp_pair.cu):
+// needs the graph's n to fit the shared-memory bitmap (pair_groups_fit) and
+// pair_groups_scratch(n, links) bytes of device scratch.
+bool pair_groups_fit(int n);
+size_t pair_groups_scratch(int n, u64 nlinks);
+cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off, const int* idx,
+                                  const Arc* arc, int cap, void* scratch, cudaStream_t st,
+                                  int* launches);
 cudaError_t launch_pair_cn(lp_link* links, const int* cnt_rows, int k, u64 n, const int* off,
                            const int* idx, const int* deg, const Arc* arc, int cap,
                            cudaStream_t st);

@@ -1,0 +1,232 @@
+// lp_pair.cu -- common-neighbour counts of the predicted pairs (AA and RA).
+//
+// The AA and RA scans accumulate fixed-point weight sums, not counts, so the
+// count |Gamma_u ∩ Gamma_v| over intermediaries b with |Gamma_b| <= L_H that
+// every predicted link reports (Section 4.1.5) is recomputed for the links the
+// selection kept.  Their top pairs join high-degree vertices, and a vertex
+// takes part in many of them, so the links are grouped by u: one CTA marks
+// Gamma_u (hub test applied) in a shared-memory bitmap over all vertices, and
+// its warps count, for every link (u, v) of the group, the marked entries of
+// Gamma_v.  Building the groups is a counting sort by u (histogram, scan,
+// scatter) in a handful of small kernels.
+#include "lp_internal.cuh"
+
+namespace lp {
+
+#define FULLMASK 0xffffffffu
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanChunk = kScanThreads * 4;  // int2 entries per block
+
+__global__ void k_pair_hist(const lp_link* __restrict__ links, u64 n, int* __restrict__ cnt) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[links[i].u], 1);
+}
+
+// Exclusive scan of the pairs v[i] (i < n) of one chunk of kScanChunk entries
+// starting at `base` (four per thread): out[i] gets the sums before i within
+// the chunk; returns the chunk total (every thread).
+__device__ __forceinline__ int2 scan_chunk(const int2 (&v)[4], int base, int n, int2* out) {
+  __shared__ int2 wsum[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int2 t = make_int2(0, 0);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    t.x += v[j].x;
+    t.y += v[j].y;
+  }
+  int2 inc = t;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int x = __shfl_up_sync(FULLMASK, inc.x, o), y = __shfl_up_sync(FULLMASK, inc.y, o);
+    if (lane >= o) {
+      inc.x += x;
+      inc.y += y;
+    }
+  }
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  const int2 w = wsum[lane];
+  int2 wi = w;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int x = __shfl_up_sync(FULLMASK, wi.x, o), y = __shfl_up_sync(FULLMASK, wi.y, o);
+    if (lane >= o) {
+      wi.x += x;
+      wi.y += y;
+    }
+  }
+  const int2 total = make_int2(__shfl_sync(FULLMASK, wi.x, 31), __shfl_sync(FULLMASK, wi.y, 31));
+  int2 run = make_int2(__shfl_sync(FULLMASK, wi.x - w.x, wid) + inc.x - t.x,
+                       __shfl_sync(FULLMASK, wi.y - w.y, wid) + inc.y - t.y);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int i = base + threadIdx.x * 4 + j;
+    if (i < n) out[i] = run;
+    run.x += v[j].x;
+    run.y += v[j].y;
+  }
+  return total;
+}
+
+// sc[i] = (links before vertex i, vertices before i with a link), chunk-local;
+// sums[chunk] = the chunk's totals.
+__global__ void __launch_bounds__(kScanThreads) k_scan_counts(const int* __restrict__ cnt, int n,
+                                                              int2* __restrict__ sc,
+                                                              int2* __restrict__ sums) {
+  const int base = blockIdx.x * kScanChunk;
+  int2 v[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int i = base + threadIdx.x * 4 + j;
+    const int c = i < n ? cnt[i] : 0;
+    v[j] = make_int2(c, c > 0 ? 1 : 0);
+  }
+  const int2 total = scan_chunk(v, base, n, sc);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// Exclusive scan of the nb <= kScanChunk chunk totals, in place (one block).
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int2* __restrict__ sums, int nb) {
+  int2 v[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int i = threadIdx.x * 4 + j;
+    v[j] = i < nb ? sums[i] : make_int2(0, 0);
+  }
+  __syncthreads();  // every value read before any is overwritten
+  scan_chunk(v, 0, nb, sums);
+}
+
+__global__ void k_scan_add(int2* __restrict__ sc, int n, const int2* __restrict__ sums) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const int2 s = sums[i / kScanChunk];
+    sc[i].x += s.x;
+    sc[i].y += s.y;
+  }
+}
+
+// groups[g] = (u, first position in perm, links of u); cnt: the histogram
+// (kept apart from the scanned array sc).
+__global__ void k_pair_groups(const int* __restrict__ cnt, const int2* __restrict__ sc, int n,
+                              int4* __restrict__ groups) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < n && cnt[u] > 0) groups[sc[u].y] = make_int4(u, sc[u].x, cnt[u], 0);
+}
+
+// perm: link indices grouped by u (the group starts in sc[u].x serve as
+// cursors; the groups were recorded before).
+__global__ void k_pair_scatter(const lp_link* __restrict__ links, u64 n, int2* __restrict__ sc,
+                               int* __restrict__ perm) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+    perm[atomicAdd(&sc[links[i].u].x, 1)] = (int)i;
+}
+
+// One group at a time per CTA (claimed from *claim): mark Gamma_u (b with
+// |Gamma_b| <= cap) in the bitmap, count the marks in Gamma_v for every link
+// of the group (a warp per link), then clear the marks.  *ngroups is the
+// total the scan left after the last vertex.
+__global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict__ links,
+                                                            const int* __restrict__ perm,
+                                                            const int4* __restrict__ groups,
+                                                            const int2* __restrict__ total,
+                                                            const int* __restrict__ off,
+                                                            const int* __restrict__ idx,
+                                                            const Arc* __restrict__ arc, int cap,
+                                                            int nwords, u32* __restrict__ claim) {
+  extern __shared__ u32 bits[];
+  __shared__ u32 s_g;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const u32 ngroups = (u32)total->y;
+  for (int i = threadIdx.x; i < nwords; i += blockDim.x) bits[i] = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_g = atomicAdd(claim, 1u);
+    __syncthreads();
+    const u32 gi = s_g;
+    if (gi >= ngroups) break;
+    const int4 G = groups[gi];
+    const int u = G.x, e0 = off[u], e1 = off[u + 1];
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const Arc t = arc[e];  // b = t.w, |Gamma_b| = t.z
+      if (t.z <= cap) atomicOr(&bits[t.w >> 5], 1u << (t.w & 31));
+    }
+    __syncthreads();
+    for (int j = wid; j < G.z; j += blockDim.x >> 5) {  // warp-uniform trips
+      const int li = perm[G.y + j];
+      const int v = links[li].v;
+      int c = 0;
+      for (int e = off[v] + lane; e < off[v + 1]; e += 32) {
+        const int b = __ldg(idx + e);
+        c += (bits[b >> 5] >> (b & 31)) & 1u;
+      }
+      c = __reduce_add_sync(FULLMASK, (u32)c);
+      if (lane == 0) links[li].cn = c;
+    }
+    __syncthreads();
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) bits[__ldg(idx + e) >> 5] = 0;
+    __syncthreads();
+  }
+}
+
+bool pair_groups_fit(int n) {
+  return n > 0 && (size_t)(n + 31) / 32 * 4 <= 224 * 1024 && (long long)n + 1 <=
+         (long long)kScanChunk * kScanChunk;
+}
+
+// Scratch layout: sc int2[n + 1], cnt int[n + 1], perm int[links], groups
+// int4[n], sums int2[chunks], claim u32; every part 256-byte aligned (groups
+// are written as int4).
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t pair_groups_scratch(int n, u64 nlinks) {
+  const size_t n1 = (size_t)n + 1;
+  return align256(n1 * sizeof(int2)) + align256(n1 * sizeof(int)) + align256(nlinks * sizeof(int)) +
+         align256((size_t)n * sizeof(int4)) +
+         align256(((n1 + kScanChunk - 1) / kScanChunk) * sizeof(int2)) + 256;
+}
+
+// Counts of links[0, n) grouped by u; scratch of pair_groups_scratch bytes.
+cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off, const int* idx,
+                                  const Arc* arc, int cap, void* scratch, cudaStream_t st,
+                                  int* launches) {
+  if (n == 0) return cudaSuccess;
+  const int n1 = nv + 1;
+  char* p = static_cast<char*>(scratch);
+  int2* sc = reinterpret_cast<int2*>(p);
+  p += align256((size_t)n1 * sizeof(int2));
+  int* cnt = reinterpret_cast<int*>(p);
+  p += align256((size_t)n1 * sizeof(int));
+  int* perm = reinterpret_cast<int*>(p);
+  p += align256(n * sizeof(int));
+  int4* groups = reinterpret_cast<int4*>(p);
+  p += align256((size_t)nv * sizeof(int4));
+  const int nb = (n1 + kScanChunk - 1) / kScanChunk;
+  int2* sums = reinterpret_cast<int2*>(p);
+  p += align256((size_t)nb * sizeof(int2));
+  u32* claim = reinterpret_cast<u32*>(p);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)n1 * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(claim, 0, sizeof(u32), st);
+  if (e != cudaSuccess) return e;
+  const int gb = (int)std::min<u64>((n + 255) / 256, 152 * 8);
+  k_pair_hist<<<gb, 256, 0, st>>>(links, n, cnt);
+  k_scan_counts<<<nb, kScanThreads, 0, st>>>(cnt, n1, sc, sums);
+  k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, nb);
+  k_scan_add<<<(n1 + 255) / 256, 256, 0, st>>>(sc, n1, sums);
+  k_pair_groups<<<(nv + 255) / 256, 256, 0, st>>>(cnt, sc, nv, groups);
+  k_pair_scatter<<<gb, 256, 0, st>>>(links, n, sc, perm);
+  const int nwords = (nv + 31) / 32;
+  const size_t smem = (size_t)nwords * 4;
+  e = cudaFuncSetAttribute(k_pair_cn_groups, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           224 * 1024);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  k_pair_cn_groups<<<nsm, 1024, smem, st>>>(links, perm, groups, sc + nv, off, idx, arc, cap,
+                                            nwords, claim);
+  if (launches) *launches += 7;
+  return cudaGetLastError();
+}
+
+}  // namespace lp
