@@ -1,0 +1,183 @@
+"""Full-size parity (needs a GPU): the configurations the benchmark and the
+serving runs use, in their launch configuration, checked on sampled outputs
+that the oracle computes one by one, and by properties that hold at any size.
+
+* R-MAT scale 20 (the benchmark graph, same seeds and hold-out), global top
+  |E^U| for JC and RA at hub limits 16, 256 and none: sampled links re-scored
+  by the oracle's pair scorer, order and pair invariants of the whole list,
+  and completeness for sampled sources (every pair of the source that ranks
+  before the last link is in the list, and nothing else of it is).
+* Chung-Lu 4,194,304 vertices and the 2048 x 2048 grid: per-source top-10
+  of every vertex for all nine measures at the paper's hub limits (4 for HP
+  and LHN, 32 for CN and AA, 256 for the rest) and IBase for JC and RA on a
+  source sample, sampled rows against the oracle.
+* R-MAT scale 24 (the serving graph): top-10 DLH(256) RA requests of 1, 300
+  and 4096 sources, sampled rows against the oracle.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import lp_inputs as L
+import oracle
+from parity import TOL, compare_sources
+
+pytestmark = pytest.mark.gpu
+
+COUNT = set(oracle.COUNT_MEASURES)
+HUB_LIMIT = {"HP": 4, "LHN": 4, "CN": 32, "AA": 32, "JC": 256, "SI": 256, "SC": 256, "HD": 256,
+             "RA": 256}
+
+
+@pytest.fixture(scope="module")
+def lp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_11415_gb300 import _build
+    _build.build()
+    import paper_2401_11415_gb300 as m
+    torch.cuda.init()
+    return m
+
+
+@pytest.fixture(scope="module")
+def rmat20():
+    return L.holdout(L.rmat(20, 16, seed=1), 0.1, seed=43)
+
+
+def _key(measure, link):
+    """Exact ordering value of an oracle link (count measures: the rational)."""
+    if measure in COUNT:
+        return Fraction(int(link["num"]), int(link["den"]))
+    return float(link["value"])
+
+
+def _ranks_before(measure, ka, ua, va, kb, ub, vb):
+    if ka != kb:
+        return ka > kb
+    return (ua, va) < (ub, vb)
+
+
+@pytest.mark.parametrize("measure", ["JC", "RA"])
+@pytest.mark.parametrize("cap", [16, 256, None])
+def test_rmat20_global_sampled(lp, rmat20, measure, cap):
+    g = rmat20.observed
+    k = len(rmat20.hu)
+    with lp.Graph.from_csr(g) as G:
+        got = G.predict(measure, cap, k)
+    assert 0 < len(got) <= k
+    u = got["u"].astype(np.int64)
+    v = got["v"].astype(np.int64)
+    assert (u < v).all() and (u >= 0).all() and (v < g.n).all()
+    assert len(np.unique(u * g.n + v)) == len(got)
+    assert (np.diff(got["score"]) <= 0).all()
+    rng = np.random.default_rng({"JC": 1000, "RA": 2000}[measure] + (cap or 0))
+    # sampled links against the pair scorer
+    for i in rng.choice(len(got), 150, replace=False).tolist() + [0, len(got) - 1]:
+        r, adj = oracle.pair(g.n, g.off, g.idx, measure, int(u[i]), int(v[i]), cap)
+        assert not adj
+        assert int(got["cn"][i]) == int(r["cn"])
+        if measure in COUNT:
+            assert got["score"][i] == np.float32(r["value"])
+        else:
+            assert abs(float(got["score"][i]) - float(r["value"])) <= TOL * float(r["value"])
+    # completeness for sampled sources against the cutoff (the last link)
+    last, _ = oracle.pair(g.n, g.off, g.idx, measure, int(u[-1]), int(v[-1]), cap)
+    kc = _key(measure, last)
+    full = len(got) < k
+    by_u = {}
+    for uu, vv in zip(u.tolist(), v.tolist()):
+        by_u.setdefault(uu, set()).add(vv)
+    deg = np.diff(g.off)
+    cand = np.nonzero(deg > 0)[0]
+    checked = 0
+    for a in rng.choice(cand, 40, replace=False).tolist() + [int(u[0])]:
+        K = 20000
+        rows, cnt = oracle.predict_sources(g.n, g.off, g.idx, measure, np.array([a], np.int32), K,
+                                           cap)
+        row = rows[0, : cnt[0]]
+        above = set()
+        for x in row:
+            c = int(x["v"])
+            if c <= a:
+                continue
+            kx = _key(measure, x)
+            if measure in COUNT:
+                if full or _ranks_before(measure, kx, a, c, kc, int(u[-1]), int(v[-1])) or \
+                        (kx == kc and (a, c) == (int(u[-1]), int(v[-1]))):
+                    above.add(c)
+            elif kx > kc * (1 + TOL):
+                above.add(c)
+        truncated = cnt[0] == K and _key(measure, row[-1]) >= kc
+        if truncated:
+            continue
+        have = by_u.get(a, set())
+        assert above <= have, (measure, cap, a, sorted(above - have)[:5])
+        if measure in COUNT:
+            assert have <= above, (measure, cap, a, sorted(have - above)[:5])
+        else:
+            for c in have - above:  # RA: only pairs within TOL of the cutoff
+                r, _ = oracle.pair(g.n, g.off, g.idx, measure, a, c, cap)
+                assert float(r["value"]) >= kc * (1 - TOL), (measure, cap, a, c)
+        checked += 1
+    assert checked >= 20
+
+
+def _per_source_check(lp, G, g, measure, cap, sources, k, sample, rng):
+    import torch
+    src = torch.tensor(sources, dtype=torch.int32, device="cuda")
+    n = len(sources)
+    out = torch.zeros((n * k * 16,), dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros((n,), dtype=torch.int32, device="cuda")
+    lp.lp_predict_sources_dev(G.handle, measure, src, n, k, cap, 0.0, out, cnt)
+    torch.cuda.synchronize()
+    links = out.cpu().numpy().view(lp.LINK_DTYPE).reshape(n, k)
+    counts = cnt.cpu().numpy()
+    pick = np.sort(rng.choice(n, min(sample, n), replace=False))
+    ol, oc = oracle.predict_sources(g.n, g.off, g.idx, measure, np.asarray(sources)[pick], k, cap)
+    compare_sources(links[pick], counts[pick], ol, oc, measure, g, np.asarray(sources)[pick], cap)
+    return counts
+
+
+@pytest.fixture(scope="module")
+def chunglu4m():
+    return L.cfg_chung_lu_4m()
+
+
+def test_chunglu4m_per_source_all_vertices(lp, chunglu4m):
+    g = chunglu4m
+    rng = np.random.default_rng(17)
+    every = np.arange(g.n, dtype=np.int32)
+    with lp.Graph.from_csr(g) as G:
+        for m in oracle.MEASURES:
+            counts = _per_source_check(lp, G, g, m, HUB_LIMIT[m], every, 10, 120, rng)
+            assert counts.max() <= 10 and counts.sum() > 0
+        sample = rng.choice(g.n, 1 << 16, replace=False).astype(np.int32)
+        for m in ("JC", "RA"):
+            _per_source_check(lp, G, g, m, None, sample, 10, 60, rng)
+        st = lp.lp_last_stats()
+        assert all(x > 0 for x in st["tier_launches"])  # every tier ran
+
+
+def test_grid_per_source_all_vertices(lp):
+    g = L.cfg_grid2048()
+    rng = np.random.default_rng(23)
+    every = np.arange(g.n, dtype=np.int32)
+    with lp.Graph.from_csr(g) as G:
+        for m in oracle.MEASURES:
+            counts = _per_source_check(lp, G, g, m, HUB_LIMIT[m], every, 10, 150, rng)
+            # every vertex of a 4-neighbour grid has second-order vertices
+            assert (counts > 0).all()
+
+
+def test_rmat24_serving_requests(lp):
+    g = L.cfg_rmat24()
+    rng = np.random.default_rng(11)
+    deg = np.diff(g.off)
+    live = np.nonzero(deg > 0)[0]
+    with lp.Graph.from_csr(g) as G:
+        for size in (1, 300, 4096):
+            sources = rng.choice(live, size, replace=False).astype(np.int32)
+            _per_source_check(lp, G, g, "RA", 256, sources, 10, 40, rng)
