@@ -161,6 +161,19 @@ lp_status lp_predict_dev(const lp_graph* g, lp_measure measure, int32_t degree_c
                          double threshold, lp_link* d_out, int64_t out_cap, int64_t* out_n);
 
 /*
+ * Global mode over a source range: as lp_predict, restricted to the pairs
+ * (u, v) with src_begin <= u < src_end (still u < v).  Sources are independent
+ * (Section 4.1.7), so the ranges of a partition of [0, n) can run on separate
+ * GPUs: the best k of the union of their lists, under the same total order,
+ * is the lp_predict result.  0 <= src_begin <= src_end <= n, else LP_EINVAL.
+ * Host output, as lp_predict.  Not in the paper (the sharding of Section 4.1.7
+ * across devices).
+ */
+lp_status lp_predict_range(const lp_graph* g, lp_measure measure, int32_t degree_cap, int64_t k,
+                           double threshold, int32_t src_begin, int32_t src_end, lp_link* out,
+                           int64_t out_cap, int64_t* out_n);
+
+/*
  * Per-source mode: for each sources[i], its k best partners c != sources[i]
  * that are not adjacent to it and score strictly above `threshold`, sorted by
  * (score desc, c asc).  out holds n_src * k links (row i for sources[i]);

@@ -87,6 +87,10 @@ def _load():
                                _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     lib.lp_predict_dev.restype = st
     lib.lp_predict_dev.argtypes = lib.lp_predict.argtypes
+    lib.lp_predict_range.restype = st
+    lib.lp_predict_range.argtypes = [_vp, ctypes.c_int, ctypes.c_int32, ctypes.c_int64,
+                                     ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _vp,
+                                     ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     lib.lp_predict_sources.restype = st
     lib.lp_predict_sources.argtypes = [_vp, ctypes.c_int, ctypes.c_int32, _vp, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.c_double, _vp, _vp]
@@ -218,6 +222,16 @@ def lp_predict(h, measure, degree_cap=None, k: int = 0, threshold: float = 0.0,
     return out[: cnt.value].copy()
 
 
+def lp_predict_range(h, measure, degree_cap, k: int, src_begin: int, src_end: int,
+                     threshold: float = 0.0):
+    """Global mode over the sources [src_begin, src_end) (host buffers)."""
+    cnt = ctypes.c_int64(0)
+    out = np.zeros(max(k, 1), dtype=LINK_DTYPE)
+    _check(_load().lp_predict_range(h, _measure(measure), _cap(degree_cap), k, threshold,
+                                    src_begin, src_end, out.ctypes.data, k, ctypes.byref(cnt)))
+    return out[: cnt.value].copy()
+
+
 def lp_predict_dev(h, measure, degree_cap, k: int, threshold: float, d_out, out_cap: int) -> int:
     """Global mode into a device buffer (torch tensor or address); returns the
     number of links found."""
@@ -293,6 +307,10 @@ class Graph:
 
     def predict(self, measure, degree_cap=None, k=0, threshold=0.0):
         return lp_predict(self.handle, measure, degree_cap, k, threshold)
+
+    def predict_range(self, measure, degree_cap, k, src_begin, src_end, threshold=0.0):
+        return lp_predict_range(self.handle, measure, degree_cap, k, src_begin, src_end,
+                                threshold)
 
     def predict_sources(self, measure, sources, k, degree_cap=None, threshold=0.0):
         return lp_predict_sources(self.handle, measure, sources, k, degree_cap, threshold)

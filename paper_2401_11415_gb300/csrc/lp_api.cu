@@ -608,19 +608,24 @@ static cudaError_t select_best(Graph& g, int measure, u64 m, u64 k, u64* n_out, 
 }
 
 static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, double threshold,
-                                lp_link* out, bool out_dev, int64_t out_cap, int64_t* out_n) {
+                                lp_link* out, bool out_dev, int64_t out_cap, int64_t* out_n,
+                                int src_begin, int src_end) {
   begin_stats();
   *out_n = 0;
   if (measure < 0 || measure > LP_RA) return fail(LP_EINVAL, "lp_predict: bad measure");
   if (k < 0) return fail(LP_EINVAL, "lp_predict: k < 0");
   if (out_cap < 0 || (out_cap > 0 && !out)) return fail(LP_EINVAL, "lp_predict: bad output buffer");
-  if (g.n == 0 || cap == 0) return LP_OK;
+  if (src_begin < 0 || src_end < src_begin || src_end > g.n)
+    return fail(LP_EINVAL, "lp_predict: source range [%d, %d) outside [0, %d)", src_begin, src_end,
+                g.n);
+  if (src_end == src_begin || cap == 0) return LP_OK;
   std::lock_guard<std::mutex> lock(g.mu);
   CU(cudaSetDevice(g.device));
   cudaStream_t st = g.stream;
   Timer tm(g);
   tm.mark(0);
   ScanArgs A = base_args(g, measure, cap, threshold, 0, 0);
+  A.rec_base = src_begin;
   // selection buffer
   const u64 minbuf = (u64)std::max<long long>(16, options_snapshot().select_buffer);
   u64 C = k > 0 ? std::max<u64>(minbuf, 2ull * (u64)k + std::min<u64>(minbuf, 1ull << 20)) : minbuf;
@@ -641,7 +646,7 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
   CU(cudaMemsetAsync(d_th, 0, sizeof(Thresh), st));
   CU(cudaMemsetAsync(g.s_flags.p, 0, (size_t)g.n + 1, st));
   Counters h{};
-  lp_status s = run_estimate(g, A, g.n, nullptr, h);
+  lp_status s = run_estimate(g, A, src_end - src_begin, nullptr, h);
   if (s != LP_OK) return s;
   tm.mark(1);
 
@@ -1012,14 +1017,22 @@ lp_status lp_predict(const lp_graph* g, lp_measure measure, int32_t degree_cap, 
                      double threshold, lp_link* out, int64_t out_cap, int64_t* out_n) {
   if (!g || !out_n) return lp::fail(LP_EINVAL, "lp_predict: null argument");
   return lp::predict_global(*const_cast<lp_graph*>(g), (int)measure, degree_cap, k, threshold, out,
-                            false, out_cap, out_n);
+                            false, out_cap, out_n, 0, g->n);
+}
+
+lp_status lp_predict_range(const lp_graph* g, lp_measure measure, int32_t degree_cap, int64_t k,
+                           double threshold, int32_t src_begin, int32_t src_end, lp_link* out,
+                           int64_t out_cap, int64_t* out_n) {
+  if (!g || !out_n) return lp::fail(LP_EINVAL, "lp_predict_range: null argument");
+  return lp::predict_global(*const_cast<lp_graph*>(g), (int)measure, degree_cap, k, threshold, out,
+                            false, out_cap, out_n, src_begin, src_end);
 }
 
 lp_status lp_predict_dev(const lp_graph* g, lp_measure measure, int32_t degree_cap, int64_t k,
                          double threshold, lp_link* d_out, int64_t out_cap, int64_t* out_n) {
   if (!g || !out_n) return lp::fail(LP_EINVAL, "lp_predict_dev: null argument");
   return lp::predict_global(*const_cast<lp_graph*>(g), (int)measure, degree_cap, k, threshold,
-                            d_out, true, out_cap, out_n);
+                            d_out, true, out_cap, out_n, 0, g->n);
 }
 
 lp_status lp_predict_sources_dev(const lp_graph* g, lp_measure measure, int32_t degree_cap,

@@ -133,6 +133,7 @@ struct ScanArgs {
   int big_span;        // dense window of a large-tier item (vertices)
   int big_bytes;       // table bytes of a large-tier CTA
   int dense16;         // global mode, count measures, degrees < 2^16: 16-bit dense counters
+  int rec_base;        // global mode: record r is source rec_base + r (a source range)
   int item_wedges;     // target wedges of one dense sweep item
   int big_threads;     // threads of a large-tier CTA: 1024 (one per SM) or 512 (two)
   u64* prof;           // optional: large-tier phase cycles (6 entries) or null

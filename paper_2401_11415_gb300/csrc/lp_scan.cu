@@ -142,8 +142,9 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
   for (int i = 0; i < 3; ++i) ts.w[i] = ts.a[i] = ts.k[i] = 0;
   ts.dense = 0;
   for (int base = gwarp * 32; base < n_rec; base += nwarps * 32) {
-    const int r = base + lane;
-    const bool valid = r < n_rec;
+    const bool valid = base + lane < n_rec;
+    // global mode: the record is the source itself (within the range)
+    const int r = MODE ? base + lane : A.rec_base + base + lane;
     int a = 0, e0 = 0, e1 = 0;
     if (valid) {
       a = MODE ? A.sources[r] : r;
