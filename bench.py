@@ -415,6 +415,93 @@ def run_serve(args):
 
 # ------------------------------------------------------- reference arm ----
 
+def run_batch(args):
+    """Batched multi-graph study: many Chung-Lu graphs (vertex counts
+    log-uniform in [1k, 500k], mean degree 8-32, exponent 2.0-2.8, seeds
+    1000 + i) packed into one lp_batch; per-source top-10 of every vertex for
+    JC (hub limit 256) and AA (hub limit 32), each query recorded once and
+    replayed, with autotuned binning; versus one plain lp_predict_sources_dev
+    call per graph on the same GPU."""
+    import torch
+    import lp_inputs as L
+    import paper_2401_11415_gb300 as lp
+    from paper_2401_11415_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(4)
+    t0 = time.perf_counter()
+    graphs = []
+    for i in range(args.graphs):
+        n = int(np.exp(rng.uniform(np.log(1000), np.log(500000))))
+        deg = float(rng.uniform(8, 32))
+        gamma = float(rng.uniform(2.0, 2.8))
+        graphs.append(L.chung_lu(n, deg, gamma, dmax=8.0 * n ** 0.5, seed=1000 + i))
+    t_gen = time.perf_counter() - t0
+    k = 10
+    queries = [("JC", 256), ("AA", 32)]
+    t0 = time.perf_counter()
+    B = lp.Batch(graphs)
+    t_pack = time.perf_counter() - t0
+    singles = [lp.Graph.from_csr(g) for g in graphs]
+    st = torch.cuda.Stream()
+    rows = []
+    for m, cap in queries:
+        default_ms, tuned_ms, opts = B.autotune(m, cap, k, repeats=2)
+        for _ in range(args.warmup):
+            B.predict_all(m, cap, k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            out, cnt = B.predict_all(m, cap, k)
+        torch.cuda.synchronize()
+        batched_s = (time.perf_counter() - t0) / args.steps
+        links = int(cnt[: B.n_total].sum().item())
+        # one plain call per graph, every vertex as a source
+        bufs = []
+        for g in graphs:
+            src = torch.arange(g.n, dtype=torch.int32, device="cuda")
+            bufs.append((src, torch.empty((max(g.n, 1) * k * 16,), dtype=torch.uint8, device="cuda"),
+                         torch.empty((max(g.n, 1),), dtype=torch.int32, device="cuda")))
+        for _ in range(max(1, args.warmup // 2)):
+            for G, g, (src, o, c) in zip(singles, graphs, bufs):
+                lp.lp_predict_sources_dev(G.handle, m, src, g.n, k, cap, 0.0, o, c)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for G, g, (src, o, c) in zip(singles, graphs, bufs):
+                lp.lp_predict_sources_dev(G.handle, m, src, g.n, k, cap, 0.0, o, c)
+        torch.cuda.synchronize()
+        plain_s = (time.perf_counter() - t0) / args.steps
+        same = all(
+            np.array_equal(bufs[i][2].cpu().numpy(),
+                           cnt[int(B.bases[i]):int(B.bases[i + 1])].cpu().numpy())
+            for i in range(len(graphs)))
+        rows.append({"query": f"{m}@{cap}", "links": links, "batched_ms": round(batched_s * 1e3, 3),
+                     "plain_ms": round(plain_s * 1e3, 3),
+                     "batched_edges_per_s": round(links / batched_s, 1),
+                     "plain_edges_per_s": round(links / plain_s, 1),
+                     "speedup": round(plain_s / batched_s, 2), "counts_identical": bool(same),
+                     "autotune": {"default_ms": round(default_ms, 3), "tuned_ms": round(tuned_ms, 3),
+                                  "options": opts}})
+    for G in singles:
+        G.close()
+    B.close()
+    tot_links = sum(r["links"] for r in rows)
+    tot_b = sum(r["batched_ms"] for r in rows) / 1e3
+    tot_p = sum(r["plain_ms"] for r in rows) / 1e3
+    return {"metric": "predicted edges/s (batched per-source top-10, JC(256) + AA(32))",
+            "value": round(tot_links / tot_b, 1), "unit": "edges/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "plain_value": round(tot_links / tot_p, 1), "speedup_vs_plain": round(tot_p / tot_b, 2),
+            "data": "synthetic",
+            "config": {"workload": f"{len(graphs)} Chung-Lu graphs, n log-uniform in [1k, 500k], "
+                                   "mean degree U[8, 32], exponent U[2.0, 2.8], seeds 1000+i",
+                       "vertices": int(sum(g.n for g in graphs)),
+                       "edges_undirected": int(sum(g.edges for g in graphs)),
+                       "generation_s": round(t_gen, 1), "pack_s": round(t_pack, 2)},
+            "queries": rows}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -492,8 +579,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only", default="", help="subset of calls, e.g. JC@inf,RA@256")
     ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (20 = the workload)")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "serve"],
-                    help="sweep: the DLH cap sweep (the benchmark line); serve: serving study")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "serve", "batch"],
+                    help="sweep: the DLH cap sweep (the benchmark line); serve: serving study; "
+                         "batch: batched multi-graph study")
+    ap.add_argument("--graphs", type=int, default=256, help="batch: number of graphs")
     ap.add_argument("--requests", type=int, default=1500, help="serve: number of requests")
     ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.9, 2.0],
                     help="serve: arrival rates as multiples of the plain capacity")
@@ -506,6 +595,8 @@ def main():
     rank, world, local = dist_init()
     if args.workload == "serve":
         line = run_serve(args) if rank == 0 else None
+    elif args.workload == "batch":
+        line = run_batch(args) if rank == 0 else None
     elif args.impl == "reference":
         line = run_reference(args, rank, world)
     else:

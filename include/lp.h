@@ -211,6 +211,39 @@ typedef enum {
                                  split targets shrink with the table) (1024)   */
 } lp_option;
 
+/*
+ * Batched multi-graph mode (not in the paper).  n_graphs independent CSR
+ * graphs (each as for lp_graph_create; host arrays, copied) are packed into
+ * one block-diagonal graph: vertex v of graph i becomes bases[i] + v, and no
+ * two-hop path crosses graphs.  lp_batch_predict_all gives the per-source
+ * top-k (as lp_predict_sources) of every packed vertex: d_out lp_link[n_total
+ * * k] and d_counts int32[n_total] on the device, pairs in packed ids (subtract
+ * bases[i] for graph i's own ids).  The first call for a (measure, degree_cap,
+ * k, output buffers, options) records the launches in a CUDA graph after one
+ * work estimate; later calls replay it.  lp_batch_autotune times replays of
+ * plans built with other binning options (tier limits, item size, large-tier
+ * CTA size), keeps the fastest for the batch (lp_batch_get_option) and
+ * reports the default and best device times of one query (ms).
+ * Errors: LP_EINVAL for bad arguments or graphs, LP_ENOMEM, LP_ECUDA,
+ * LP_EINTERNAL if a device check fails.
+ */
+typedef struct lp_batch lp_batch;
+lp_status lp_batch_create(int32_t n_graphs, const int32_t* n_vertices,
+                          const int32_t* const* offsets, const int32_t* const* indices,
+                          uint32_t flags, lp_batch** out);
+lp_status lp_batch_destroy(lp_batch* b);
+/* n_graphs, n_total and bases (int32[n_graphs + 1]) of a batch; any may be null. */
+lp_status lp_batch_info(const lp_batch* b, int32_t* n_graphs, int32_t* n_total, int32_t* bases);
+/* The packed graph (for lp_graph_info, lp_predict_sources, ...); owned by the batch. */
+const lp_graph* lp_batch_graph(const lp_batch* b);
+lp_status lp_batch_predict_all(lp_batch* b, lp_measure measure, int32_t degree_cap, int32_t k,
+                               lp_link* d_out, int32_t* d_counts);
+lp_status lp_batch_autotune(lp_batch* b, lp_measure measure, int32_t degree_cap, int32_t k,
+                            int32_t repeats, lp_link* d_out, int32_t* d_counts, float* default_ms,
+                            float* best_ms);
+/* The batch's value of a binning option (-1 for others). */
+int64_t lp_batch_get_option(const lp_batch* b, lp_option option);
+
 /* Set a tuning option; LP_EINVAL if the option or value is out of range. */
 lp_status lp_set_option(lp_option option, int64_t value);
 

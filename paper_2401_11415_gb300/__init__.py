@@ -87,6 +87,24 @@ def _load():
                                _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     lib.lp_predict_dev.restype = st
     lib.lp_predict_dev.argtypes = lib.lp_predict.argtypes
+    lib.lp_batch_create.restype = st
+    lib.lp_batch_create.argtypes = [ctypes.c_int32, _vp, _vp, _vp, ctypes.c_uint32,
+                                    ctypes.POINTER(_vp)]
+    lib.lp_batch_destroy.restype = st
+    lib.lp_batch_destroy.argtypes = [_vp]
+    lib.lp_batch_info.restype = st
+    lib.lp_batch_info.argtypes = [_vp, _i32p, _i32p, _vp]
+    lib.lp_batch_graph.restype = _vp
+    lib.lp_batch_graph.argtypes = [_vp]
+    lib.lp_batch_predict_all.restype = st
+    lib.lp_batch_predict_all.argtypes = [_vp, ctypes.c_int, ctypes.c_int32, ctypes.c_int32, _vp,
+                                         _vp]
+    lib.lp_batch_autotune.restype = st
+    lib.lp_batch_autotune.argtypes = [_vp, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32, _vp, _vp, ctypes.POINTER(ctypes.c_float),
+                                      ctypes.POINTER(ctypes.c_float)]
+    lib.lp_batch_get_option.restype = ctypes.c_int64
+    lib.lp_batch_get_option.argtypes = [_vp, ctypes.c_int]
     lib.lp_predict_range.restype = st
     lib.lp_predict_range.argtypes = [_vp, ctypes.c_int, ctypes.c_int32, ctypes.c_int64,
                                      ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _vp,
@@ -335,6 +353,85 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+# -------------------------------------------------------- batched mode --
+
+class Batch:
+    """Many graphs packed into one block-diagonal graph (lp_batch_*): the
+    per-source top-k of every vertex of every graph from one recorded launch
+    sequence.  ``predict_all`` fills device buffers (torch tensors) and
+    returns them with packed ids; ``bases[i]`` is graph i's first vertex."""
+
+    def __init__(self, graphs, flags: int = 0):
+        lib = _load()
+        ng = len(graphs)
+        self._keep = [(np.ascontiguousarray(g.off, dtype=np.int32),
+                       np.ascontiguousarray(g.idx, dtype=np.int32)) for g in graphs]
+        nv = np.array([g.n for g in graphs], dtype=np.int32)
+        offs = (ctypes.c_void_p * ng)(*[o.ctypes.data for o, _ in self._keep])
+        idxs = (ctypes.c_void_p * ng)(*[(i.ctypes.data if i.size else o.ctypes.data)
+                                        for o, i in self._keep])
+        h = _vp()
+        _check(lib.lp_batch_create(ng, nv.ctypes.data, ctypes.cast(offs, _vp),
+                                   ctypes.cast(idxs, _vp), flags, ctypes.byref(h)))
+        self.handle = h
+        self._keep = None
+        ngr, nt = ctypes.c_int32(0), ctypes.c_int32(0)
+        self.bases = np.zeros(ng + 1, dtype=np.int32)
+        _check(lib.lp_batch_info(h, ctypes.byref(ngr), ctypes.byref(nt), self.bases.ctypes.data))
+        self.n_graphs, self.n_total = ngr.value, nt.value
+        self._out = None
+
+    def close(self):
+        if self.handle:
+            _load().lp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def graph_handle(self):
+        return _load().lp_batch_graph(self.handle)
+
+    def _buffers(self, k):
+        import torch
+        if self._out is None or self._out[2] != k:
+            out = torch.empty((max(self.n_total, 1) * k * 16,), dtype=torch.uint8, device="cuda")
+            cnt = torch.empty((max(self.n_total, 1),), dtype=torch.int32, device="cuda")
+            self._out = (out, cnt, k)
+        return self._out[0], self._out[1]
+
+    def predict_all(self, measure, degree_cap=None, k: int = 10):
+        """(links uint8 device tensor of n_total * k LINK_DTYPE rows, counts)."""
+        out, cnt = self._buffers(k)
+        _check(_load().lp_batch_predict_all(self.handle, _measure(measure), _cap(degree_cap), k,
+                                            _ptr(out), _ptr(cnt)))
+        return out, cnt
+
+    def autotune(self, measure, degree_cap=None, k: int = 10, repeats: int = 2):
+        """Tune the batch's binning options on this query; returns
+        (default_ms, best_ms, {option: value})."""
+        out, cnt = self._buffers(k)
+        d, b = ctypes.c_float(0), ctypes.c_float(0)
+        _check(_load().lp_batch_autotune(self.handle, _measure(measure), _cap(degree_cap), k,
+                                         repeats, _ptr(out), _ptr(cnt), ctypes.byref(d),
+                                         ctypes.byref(b)))
+        names = {"warp_max": LP_OPT_WARP_MAX_WEDGES, "med_max": LP_OPT_MED_MAX_WEDGES,
+                 "cta_max": LP_OPT_CTA_MAX_WEDGES, "item_wedges": LP_OPT_ITEM_WEDGES,
+                 "big_threads": LP_OPT_BIG_CTA_THREADS}
+        opts = {nm: int(_load().lp_batch_get_option(self.handle, o)) for nm, o in names.items()}
+        return d.value, b.value, opts
 
 
 # ------------------------------------------------------------- serving --

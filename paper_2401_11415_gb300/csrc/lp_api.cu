@@ -68,7 +68,7 @@ static lp_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 // Grow a scratch allocation to at least `bytes` (contents are not kept).
-static cudaError_t ensure(Graph& g, Graph::Scratch& s, size_t bytes) {
+cudaError_t ensure(Graph& g, Graph::Scratch& s, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (s.bytes >= bytes) return cudaSuccess;
   if (s.p) {
@@ -89,10 +89,6 @@ static cudaError_t ensure(Graph& g, Graph::Scratch& s, size_t bytes) {
   return cudaSuccess;
 }
 
-template <typename T>
-static T* sp(Graph::Scratch& s) {
-  return reinterpret_cast<T*>(s.p);
-}
 
 // ------------------------------------------------------ graph residency --
 
@@ -434,9 +430,13 @@ static void estimate_stats(const Counters& h) {
 }
 
 static ScanArgs base_args(Graph& g, int measure, int cap, double threshold, int mode, int k) {
+  return base_args_opts(g, measure, cap, threshold, mode, k, options_snapshot());
+}
+
+ScanArgs base_args_opts(Graph& g, int measure, int cap, double threshold, int mode, int k,
+                        const Options& o) {
   ScanArgs A;
   memset(&A, 0, sizeof(A));
-  const Options o = options_snapshot();
   const bool v64 = measure == LP_AA || measure == LP_RA;
   const int vbytes = v64 ? 8 : 4;
   const int bt = o.big_threads;

@@ -39,6 +39,7 @@ constexpr int kSmemPerCtaReserved = 1024;
 // Item kinds (int4.w of a CTA work record).
 constexpr int kItemDense = 1;    // dense counters over [lo, hi)
 constexpr int kItemSingle = 2;   // the only item of its source (per-source mode)
+constexpr int kItemWhole = 4;    // one item covers the source's whole second-order id range
 
 // Arc table entry for arc e = (a -> b): x = position of a in Gamma_b
 // (absolute index into idx), y = off[b + 1], z = |Gamma_b|, w = b.
@@ -134,6 +135,8 @@ struct ScanArgs {
   int big_bytes;       // table bytes of a large-tier CTA
   int dense16;         // global mode, count measures, degrees < 2^16: 16-bit dense counters
   int rec_base;        // global mode: record r is source rec_base + r (a source range)
+  int no_split;        // per-source mode: large sources become dense items (no hash overflow)
+  int partial_by_item; // per-source mode: an item's partial list goes to slot = its queue index
   int item_wedges;     // target wedges of one dense sweep item
   int big_threads;     // threads of a large-tier CTA: 1024 (one per SM) or 512 (two)
   u64* prof;           // optional: large-tier phase cycles (6 entries) or null
@@ -249,6 +252,15 @@ void stats_begin();
 void stats_estimate(const Counters& h);
 void stats_add(int64_t candidates, int32_t splits, int32_t launches);
 ScanArgs scan_args(Graph& g, int measure, int cap, double threshold, int mode, int k);
+// scan_args with explicit options instead of the process-wide ones
+ScanArgs base_args_opts(Graph& g, int measure, int cap, double threshold, int mode, int k,
+                        const Options& o);
+// Grow a scratch allocation to at least `bytes` (contents are not kept).
+cudaError_t ensure(Graph& g, Graph::Scratch& s, size_t bytes);
+template <typename T>
+inline T* sp(Graph::Scratch& s) {
+  return reinterpret_cast<T*>(s.p);
+}
 lp_status sources_args_ok(const lp_graph* g, int measure, const void* sources, int n_src, int k,
                           const void* out, const void* counts);
 Graph& graph_of(const lp_graph* g);

@@ -153,6 +153,16 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
     }
     u64 W = 0;
     u32 kept = 0;
+    // the second-order ids span [nlo, nhi]: each kept list (or suffix) is
+    // sorted, so its first and last ids bound it
+    int nlo = INT_MAX, nhi = -1;
+    auto span_arc = [&](const Arc& t, int& l, int& h) {
+      const int s0 = MODE ? t.y - t.z : t.x + 1;
+      if (s0 < t.y) {
+        l = min(l, __ldg(A.idx + s0));
+        h = max(h, __ldg(A.idx + t.y - 1));
+      }
+    };
     const bool small = valid && (e1 - e0) <= 64;
     if (small) {
       for (int e = e0; e < e1; ++e) {
@@ -160,6 +170,7 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
         if (t.z <= A.cap) {
           W += MODE ? (u64)(t.z - 1) : (u64)(t.y - t.x - 1);
           ++kept;
+          span_arc(t, nlo, nhi);
         }
       }
     }
@@ -170,11 +181,13 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
       const int j0 = __shfl_sync(FULLMASK, e0, j), j1 = __shfl_sync(FULLMASK, e1, j);
       u64 Wj = 0;
       u32 kj = 0;
+      int lj = INT_MAX, hj = -1;
       for (int e = j0 + lane; e < j1; e += 32) {
         const Arc t = A.arc[e];
         if (t.z <= A.cap) {
           Wj += MODE ? (u64)(t.z - 1) : (u64)(t.y - t.x - 1);
           ++kj;
+          span_arc(t, lj, hj);
         }
       }
 #pragma unroll
@@ -182,14 +195,18 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
         Wj += __shfl_xor_sync(FULLMASK, Wj, o);
         kj += __shfl_xor_sync(FULLMASK, kj, o);
       }
+      lj = __reduce_min_sync(FULLMASK, lj);
+      hj = __reduce_max_sync(FULLMASK, hj);
       if (lane == j) {
         W = Wj;
         kept = kj;
+        nlo = lj;
+        nhi = hj;
       }
     }
-    // binning
-    const int lo = MODE ? 0 : a + 1;
-    const int hi = A.n;
+    // binning (items cover only the source's second-order id range)
+    const int lo = W > 0 ? max(MODE ? 0 : a + 1, nlo) : (MODE ? 0 : a + 1);
+    const int hi = W > 0 ? min(A.n, nhi + 1) : A.n;
     int tier = -1;
     if (valid && W > 0) tier = W <= (u64)A.warp_max ? 0 : (W <= (u64)A.med_max ? 1 : 2);
     if (tier >= 0) {
@@ -223,7 +240,8 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
         if (tier == 1) {
           const int logcap = max(6, min(11, ceil_log2(2 * W)));
           const int kind = MODE ? kItemSingle : 0;
-          medq[q + __popc(m & lt)] = make_int4(r, lo, hi, kind | (logcap << 8) | (1 << 29));
+          medq[q + __popc(m & lt)] =
+              make_int4(r, lo, hi, kind | kItemWhole | (logcap << 8) | (1 << 29));
         }
       }
     }
@@ -242,7 +260,7 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
         const double cost_d =
             (double)sd * (kept * 2.0 + A.big_span / 8.0) + (double)W + (double)pdi * kept * 24.0;
         logcap = A.split_logcap;
-        if (cost_d < cost_h) {
+        if (cost_d < cost_h || A.no_split) {  // dense items never overflow
           Gd = (int)((sd + pdi - 1) / pdi);
           P = (int)((sd + Gd - 1) / Gd);
           kind = kItemDense;
@@ -251,6 +269,7 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
         }
       }
       if (MODE && P == 1) kind |= kItemSingle;
+      if (P == 1) kind |= kItemWhole;
       if (kind & kItemDense) ts.dense += (u64)P;
     }
     int incl = P;
@@ -1144,7 +1163,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 8)) k_scan_cta(
     const int logcap = (rec.w >> 8) & 0xff;
     const int nslots = 1 << logcap;
     const int limit = (nslots * 3) / 4;
-    const bool full_range = (lo <= (MODE ? 0 : a + 1)) && hi >= A.n;
+    const bool full_range = (rec.w & kItemWhole) || ((lo <= (MODE ? 0 : a + 1)) && hi >= A.n);
     const int span = hi - lo;
     const int e0 = A.off[a], e1 = A.off[a + 1];
     for (int eb = e0 + wid * 32; eb < e1; eb += NW * 32) {
@@ -1264,7 +1283,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 8)) k_scan_cta(
           if (lane == 0) A.out_cnt[r] = cnt;
         } else {
           u64 p = 0;
-          if (lane == 0) p = atomicAdd(&A.ctr->npartial, 1ull);
+          if (lane == 0) p = A.partial_by_item ? qi : atomicAdd(&A.ctr->npartial, 1ull);
           p = __shfl_sync(FULLMASK, p, 0);
           if (p < A.partial_cap) {
             for (int j = lane; j < cnt; j += 32) A.partial[p * A.k + j] = top[j];
@@ -1471,7 +1490,8 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
     for (int g = 0; g < G; ++g) {
       const int lg = lo + (int)(((u64)span * (u64)g) / (u64)G);
       const int hg = lo + (int)(((u64)span * (u64)(g + 1)) / (u64)G);
-      const bool full_range = G == 1 && lo <= (MODE ? 0 : a + 1) && hi >= A.n;
+      const bool full_range =
+          G == 1 && ((rec.w & kItemWhole) || (lo <= (MODE ? 0 : a + 1) && hi >= A.n));
       if (threadIdx.x == 0) {
         s_ndistinct = 0;
         s_overflow = 0;
@@ -1706,7 +1726,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
           if (lane == 0) A.out_cnt[r] = cnt;
         } else {
           u64 p = 0;
-          if (lane == 0) p = atomicAdd(&A.ctr->npartial, 1ull);
+          if (lane == 0) p = A.partial_by_item ? qi : atomicAdd(&A.ctr->npartial, 1ull);
           p = __shfl_sync(FULLMASK, p, 0);
           if (p < A.partial_cap) {
             for (int j = lane; j < cnt; j += 32) A.partial[p * A.k + j] = top[j];
