@@ -69,7 +69,15 @@ def test_batch_equals_each_graph_alone(lp, graphs, measure, cap):
             with lp.Graph.from_csr(g) as G:
                 el, ec = G.predict_sources(measure, np.arange(g.n, dtype=np.int32), k, cap)
             assert np.array_equal(gc, ec), (measure, i)
-            assert gl.tobytes() == el.tobytes(), (measure, i)
+            if measure in ("AA", "RA"):
+                # the packed graph's larger max degree may pick another
+                # fixed-point scale, so near-equal sums can swap: every row
+                # is checked against the oracle within the AA/RA tolerance
+                every = np.arange(g.n, dtype=np.int32)
+                ol, oc = oracle.predict_sources(g.n, g.off, g.idx, measure, every, k, cap)
+                compare_sources(gl, gc, ol, oc, measure, g, every, cap)
+            else:
+                assert gl.tobytes() == el.tobytes(), (measure, i)
             if i in (0, 3):
                 rng = np.random.default_rng(i)
                 pick = np.sort(rng.choice(g.n, min(40, g.n), replace=False)).astype(np.int32)
