@@ -913,6 +913,41 @@ __device__ __forceinline__ bool score_dense_linear(const ScanArgs& A, const Thre
   return fail;
 }
 
+// The same for 64-bit counters kept as two arrays of 32-bit halves (position
+// p: low word lo[p], high word hi[p]), so the low-word atomics of the scan
+// spread over all banks.
+__device__ __forceinline__ bool score_dense64_linear(const ScanArgs& A, const Thresh& T, int a,
+                                                     u64 da, u32* lo, u32* hi, int base0, int npos,
+                                                     int lg, u64 vmin, u64& n_cand, int& qn,
+                                                     int& qc, u64& qv, int& qd) {
+  const int base = base0 + lane_id() * 4;
+  uint4 l4 = make_uint4(0, 0, 0, 0), h4 = make_uint4(0, 0, 0, 0);
+  if (base < npos) {
+    l4 = *reinterpret_cast<const uint4*>(lo + base);
+    h4 = *reinterpret_cast<const uint4*>(hi + base);
+    if ((l4.x | l4.y | l4.z | l4.w | h4.x | h4.y | h4.z | h4.w) != 0) {
+      *reinterpret_cast<uint4*>(lo + base) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(hi + base) = make_uint4(0, 0, 0, 0);
+    }
+  }
+  const u64 v4[4] = {(u64)l4.x | ((u64)h4.x << 32), (u64)l4.y | ((u64)h4.y << 32),
+                     (u64)l4.z | ((u64)h4.z << 32), (u64)l4.w | ((u64)h4.w << 32)};
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    n_cand += v4[j] != 0 ? 1 : 0;
+    any |= v4[j] != 0 && v4[j] >= vmin;
+  }
+  if (!__any_sync(FULLMASK, any)) return false;
+  bool fail = false;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const bool live = v4[j] != 0 && v4[j] >= vmin;
+    fail |= survivors_push<u64>(A, T, a, da, live, lg + swz(base + j), v4[j], qn, qc, qv, qd);
+  }
+  return fail;
+}
+
 // The same for 16-bit counters, two per word (count measures, counts below
 // 2^16): 256 positions per warp, eight per lane.
 __device__ __forceinline__ bool score_dense16_linear(const ScanArgs& A, const Thresh& T, int a,
@@ -1428,8 +1463,11 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
 
   const int lane = lane_id();
   const int wid = threadIdx.x >> 5;
-  // global mode, count measures: dense windows of 16-bit counters
+  // global mode, count measures: dense windows of 16-bit counters; AA / RA:
+  // 64-bit counters as two arrays of halves (low words, then high words)
   const bool d16 = MODE == 0 && !V64 && A.dense16;
+  u32* dlo = reinterpret_cast<u32*>(smem);
+  u32* dhi = dlo + A.big_span;
   for (int i = threadIdx.x * 16; i < table_bytes; i += THREADS * 16)
     *reinterpret_cast<int4*>(smem + i) = make_int4(0, 0, 0, 0);
   Thresh T;
@@ -1505,8 +1543,12 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
         if (is_dense) {
           const int i = c - lg;
           if (MODE == 0) {  // scored by a linear scan: no touched bits
-            if (sizeof(V) == 8) {
-              shared_add<V>(&dense[swz(i)], wc);
+            if (sizeof(V) == 8) {  // split halves: low word, then high word plus carry
+              const int p = swz(i);
+              const u32 l = (u32)wc, h = (u32)((u64)wc >> 32);
+              const u32 old = atomicAdd(dlo + p, l);
+              const u32 hc = h + ((old + l < old) ? 1u : 0u);
+              if (hc) atomicAdd(dhi + p, hc);
             } else if (d16) {  // count measures: the weight is 1
               const int p = swz(i);
               atomicAdd(reinterpret_cast<u32*>(dense) + (p >> 1), 1u << ((p & 1) << 4));
@@ -1646,6 +1688,10 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
         if (is_dense && d16) {
           const int p = swz(b - lg);
           atomicAnd(reinterpret_cast<u32*>(dense) + (p >> 1), ~(0xffffu << ((p & 1) << 4)));
+        } else if (is_dense && MODE == 0 && V64) {
+          const int p = swz(b - lg);
+          dlo[p] = 0;
+          dhi[p] = 0;
         } else if (is_dense) {
           dense[swz(b - lg)] = 0;
         }
@@ -1665,6 +1711,13 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
             fail |= score_dense16_linear(A, T, a, da, reinterpret_cast<u32*>(dense), base0, npos,
                                          lg, vmin, n_cand, qn, qc, qv16, qd);
           qv = (V)qv16;
+        } else if (is_dense && V64) {
+          const int npos = (hg - lg + 31) & ~31;
+          u64 qv64 = (u64)qv;
+          for (int base0 = wid * 128; base0 < npos; base0 += THREADS * 4)  // warp-uniform trips
+            fail |= score_dense64_linear(A, T, a, da, dlo, dhi, base0, npos, lg, vmin, n_cand, qn,
+                                         qc, qv64, qd);
+          qv = (V)qv64;
         } else if (is_dense) {
           const int npos = (hg - lg + 31) & ~31;
           for (int base0 = wid * 128; base0 < npos; base0 += THREADS * 4)  // warp-uniform trips
