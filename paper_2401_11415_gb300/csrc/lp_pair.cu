@@ -156,7 +156,15 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
       const int li = perm[G.y + j];
       const int v = links[li].v;
       int c = 0;
-      for (int e = off[v] + lane; e < off[v + 1]; e += 32) {
+      const int ee = off[v + 1];
+      int e = off[v] + lane;
+      for (; e + 96 < ee; e += 128) {  // four loads in flight per lane
+        const int b0 = __ldg(idx + e), b1 = __ldg(idx + e + 32), b2 = __ldg(idx + e + 64),
+                  b3 = __ldg(idx + e + 96);
+        c += ((bits[b0 >> 5] >> (b0 & 31)) & 1u) + ((bits[b1 >> 5] >> (b1 & 31)) & 1u) +
+             ((bits[b2 >> 5] >> (b2 & 31)) & 1u) + ((bits[b3 >> 5] >> (b3 & 31)) & 1u);
+      }
+      for (; e < ee; e += 32) {
         const int b = __ldg(idx + e);
         c += (bits[b >> 5] >> (b & 31)) & 1u;
       }
