@@ -246,24 +246,28 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
       }
     }
     // large tier: P items per source
-    int P = 0, kind = 0, logcap = 0, Gd = 1;
+    int P = 0, kind = 0, logcap = 0, Gd = 1, bspan = A.big_span;
     if (tier == 2) {
       const u64 span = (u64)(hi - lo);
       if (W <= (u64)A.cta_max) {
         P = 1;
         logcap = max(10, ceil_log2(2 * W));
       } else {
+        // 16-bit dense counters hold twice as many 8-bit ones; a count never
+        // exceeds the kept arcs of the source
+        const bool d8 = MODE == 0 && A.dense16 && kept <= 255;
+        bspan = d8 ? 2 * A.big_span : A.big_span;
         const u64 sh = (W + A.split_target - 1) / A.split_target;
-        const u64 sd = (span + A.big_span - 1) / A.big_span;
+        const u64 sd = (span + bspan - 1) / bspan;
         const u64 pdi = max((u64)1, min(sd, (W + A.item_wedges - 1) / A.item_wedges));
         const double cost_h = (double)sh * (kept * 24.0 + (1 << A.split_logcap) / 4.0) + W * 3.0;
         const double cost_d =
-            (double)sd * (kept * 2.0 + A.big_span / 8.0) + (double)W + (double)pdi * kept * 24.0;
+            (double)sd * (kept * 2.0 + bspan / 8.0) + (double)W + (double)pdi * kept * 24.0;
         logcap = A.split_logcap;
         if (cost_d < cost_h || A.no_split) {  // dense items never overflow
           Gd = (int)((sd + pdi - 1) / pdi);
           P = (int)((sd + Gd - 1) / Gd);
-          kind = kItemDense;
+          kind = kItemDense | (d8 ? kItemD8 : 0);
         } else {
           P = (int)min(sh, span);
         }
@@ -291,9 +295,9 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
           int l2, h2;
           int gcount = 1;
           if (kind & kItemDense) {
-            l2 = lo + (int)min(span, (u64)p * Gd * A.big_span);
-            h2 = lo + (int)min(span, (u64)(p + 1) * Gd * A.big_span);
-            gcount = (h2 - l2 + A.big_span - 1) / A.big_span;
+            l2 = lo + (int)min(span, (u64)p * Gd * bspan);
+            h2 = lo + (int)min(span, (u64)(p + 1) * Gd * bspan);
+            gcount = (h2 - l2 + bspan - 1) / bspan;
           } else {
             l2 = lo + (int)((span * (u64)p) / (u64)P);
             h2 = lo + (int)((span * (u64)(p + 1)) / (u64)P);
@@ -913,6 +917,36 @@ __device__ __forceinline__ bool score_dense_linear(const ScanArgs& A, const Thre
   return fail;
 }
 
+// The same for 8-bit counters, four per word (sources of degree <= 255): 256
+// positions per warp, eight per lane.
+__device__ __forceinline__ bool score_dense8_linear(const ScanArgs& A, const Thresh& T, int a,
+                                                    u64 da, u32* words, int base0, int npos,
+                                                    int lg, u64 vmin, u64& n_cand, int& qn,
+                                                    int& qc, u32& qv, int& qd) {
+  const int base = base0 + lane_id() * 8;
+  uint2 w = make_uint2(0, 0);
+  if (base < npos) {
+    w = *reinterpret_cast<const uint2*>(words + (base >> 2));
+    if ((w.x | w.y) != 0) *reinterpret_cast<uint2*>(words + (base >> 2)) = make_uint2(0, 0);
+  }
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const u32 v = ((j < 4 ? w.x : w.y) >> ((j & 3) << 3)) & 0xffu;
+    n_cand += v != 0 ? 1 : 0;
+    any |= v != 0 && (u64)v >= vmin;
+  }
+  if (!__any_sync(FULLMASK, any)) return false;
+  bool fail = false;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const u32 v = ((j < 4 ? w.x : w.y) >> ((j & 3) << 3)) & 0xffu;
+    const bool live = v != 0 && (u64)v >= vmin;
+    fail |= survivors_push<u32>(A, T, a, da, live, lg + swz(base + j), v, qn, qc, qv, qd);
+  }
+  return fail;
+}
+
 // The same for 64-bit counters kept as two arrays of 32-bit halves (position
 // p: low word lo[p], high word hi[p]), so the low-word atomics of the scan
 // spread over all banks.
@@ -1496,6 +1530,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
     const int a = MODE ? A.sources[r] : r;
     const int lo = rec.y, hi = rec.z;
     const bool is_dense = (rec.w & kItemDense) != 0;
+    const bool d8 = d16 && (rec.w & kItemD8) != 0;  // 8-bit counters for this item
     const int logcap = (rec.w >> 8) & 0xff;
     const int G = is_dense ? ((rec.w >> 16) & 0xfff) + 1 : 1;
     const int nslots = 1 << logcap;
@@ -1549,7 +1584,10 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
               const u32 old = atomicAdd(dlo + p, l);
               const u32 hc = h + ((old + l < old) ? 1u : 0u);
               if (hc) atomicAdd(dhi + p, hc);
-            } else if (d16) {  // count measures: the weight is 1
+            } else if (d8) {  // count measures: the weight is 1
+              const int p = swz(i);
+              atomicAdd(reinterpret_cast<u32*>(dense) + (p >> 2), 1u << ((p & 3) << 3));
+            } else if (d16) {
               const int p = swz(i);
               atomicAdd(reinterpret_cast<u32*>(dense) + (p >> 1), 1u << ((p & 1) << 4));
             } else {
@@ -1685,7 +1723,10 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
       for (int e = e0 + threadIdx.x; e < e1; e += THREADS) {
         const int b = __ldg(A.idx + e);
         if (b < lg || b >= hg || (MODE == 0 && b <= a)) continue;
-        if (is_dense && d16) {
+        if (is_dense && d8) {
+          const int p = swz(b - lg);
+          atomicAnd(reinterpret_cast<u32*>(dense) + (p >> 2), ~(0xffu << ((p & 3) << 3)));
+        } else if (is_dense && d16) {
           const int p = swz(b - lg);
           atomicAnd(reinterpret_cast<u32*>(dense) + (p >> 1), ~(0xffffu << ((p & 1) << 4)));
         } else if (is_dense && MODE == 0 && V64) {
@@ -1704,7 +1745,14 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
       if (MODE == 0 && (is_dense || T.valid)) {
         int qn = 0, qc = 0, qd = 0;
         V qv = 0;
-        if (is_dense && d16) {
+        if (is_dense && d8) {
+          const int npos = (hg - lg + 31) & ~31;
+          u32 qv8 = (u32)qv;
+          for (int base0 = wid * 256; base0 < npos; base0 += THREADS * 8)  // warp-uniform trips
+            fail |= score_dense8_linear(A, T, a, da, reinterpret_cast<u32*>(dense), base0, npos,
+                                        lg, vmin, n_cand, qn, qc, qv8, qd);
+          qv = (V)qv8;
+        } else if (is_dense && d16) {
           const int npos = (hg - lg + 31) & ~31;
           u32 qv16 = (u32)qv;
           for (int base0 = wid * 256; base0 < npos; base0 += THREADS * 8)  // warp-uniform trips
