@@ -917,6 +917,23 @@ __device__ __forceinline__ bool score_dense_linear(const ScanArgs& A, const Thre
   return fail;
 }
 
+// Lane-parallel tests on packed counters (SWAR).  nonzero8 / nonzero16: the
+// number of nonzero 8-bit / 16-bit lanes of x (a lane's low bits plus the
+// all-ones low mask reach its top bit iff they are nonzero; OR-ing x covers a
+// set top bit; no carry leaves the lane).  any_ge8: whether some 8-bit lane
+// of x is >= m (1 <= m <= 256): every byte, widened to a 16-bit lane, plus
+// 256 - m reaches bit 8 iff byte >= m, and stays below 2^16.
+__device__ __forceinline__ int nonzero8(u32 x) {
+  return __popc((((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x) & 0x80808080u);
+}
+__device__ __forceinline__ int nonzero16(u32 x) {
+  return __popc((((x & 0x7fff7fffu) + 0x7fff7fffu) | x) & 0x80008000u);
+}
+__device__ __forceinline__ bool any_ge8(u32 x, u32 cth) {
+  const u32 e = x & 0x00ff00ffu, o = (x >> 8) & 0x00ff00ffu;
+  return (((e + cth) | (o + cth)) & 0x01000100u) != 0;
+}
+
 // The same for 8-bit counters, four per word (sources of degree <= 255): 256
 // positions per warp, eight per lane.
 __device__ __forceinline__ bool score_dense8_linear(const ScanArgs& A, const Thresh& T, int a,
@@ -929,19 +946,15 @@ __device__ __forceinline__ bool score_dense8_linear(const ScanArgs& A, const Thr
     w = *reinterpret_cast<const uint2*>(words + (base >> 2));
     if ((w.x | w.y) != 0) *reinterpret_cast<uint2*>(words + (base >> 2)) = make_uint2(0, 0);
   }
-  bool any = false;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const u32 v = ((j < 4 ? w.x : w.y) >> ((j & 3) << 3)) & 0xffu;
-    n_cand += v != 0 ? 1 : 0;
-    any |= v != 0 && (u64)v >= vmin;
-  }
-  if (!__any_sync(FULLMASK, any)) return false;
+  n_cand += (u64)(nonzero8(w.x) + nonzero8(w.y));
+  const u32 m = (u32)min(max(vmin, (u64)1), (u64)256);  // counters are nonzero and below 256
+  const u32 cth = (256u - m) * 0x00010001u;
+  if (!__any_sync(FULLMASK, any_ge8(w.x, cth) || any_ge8(w.y, cth))) return false;
   bool fail = false;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const u32 v = ((j < 4 ? w.x : w.y) >> ((j & 3) << 3)) & 0xffu;
-    const bool live = v != 0 && (u64)v >= vmin;
+    const bool live = v >= m;
     fail |= survivors_push<u32>(A, T, a, da, live, lg + swz(base + j), v, qn, qc, qv, qd);
   }
   return fail;
@@ -995,20 +1008,17 @@ __device__ __forceinline__ bool score_dense16_linear(const ScanArgs& A, const Th
     if ((w.x | w.y | w.z | w.w) != 0)
       *reinterpret_cast<uint4*>(words + (base >> 1)) = make_uint4(0, 0, 0, 0);
   }
+  n_cand += (u64)(nonzero16(w.x) + nonzero16(w.y) + nonzero16(w.z) + nonzero16(w.w));
+  const u32 m = (u32)min(max(vmin, (u64)1), (u64)65536);  // counters are nonzero
+  auto top = [](u32 x) { return max(x & 0xffffu, x >> 16); };
+  if (!__any_sync(FULLMASK, max(max(top(w.x), top(w.y)), max(top(w.z), top(w.w))) >= m))
+    return false;
   const u32 ww[4] = {w.x, w.y, w.z, w.w};
-  bool any = false;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const u32 v = (ww[j >> 1] >> ((j & 1) << 4)) & 0xffffu;
-    n_cand += v != 0 ? 1 : 0;
-    any |= v != 0 && (u64)v >= vmin;
-  }
-  if (!__any_sync(FULLMASK, any)) return false;
   bool fail = false;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const u32 v = (ww[j >> 1] >> ((j & 1) << 4)) & 0xffffu;
-    const bool live = v != 0 && (u64)v >= vmin;
+    const bool live = v >= m;
     fail |= survivors_push<u32>(A, T, a, da, live, lg + swz(base + j), v, qn, qc, qv, qd);
   }
   return fail;
