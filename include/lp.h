@@ -197,8 +197,9 @@ typedef enum {
                                  (default 8388608; 24 bytes each, twice)       */
   LP_OPT_WARP_MAX_WEDGES = 2, /* warp tier: sources with W <= this (1..256, 256) */
   LP_OPT_CTA_MAX_WEDGES = 3,  /* one large item per source up to W (257..8192, 8192) */
-  LP_OPT_SPLIT_TARGET = 4,    /* wedges per split hash item (256..12288, 6144),
-                                 halved per log2 step the table is below LOGCAP */
+  LP_OPT_SPLIT_TARGET = 4,    /* wedges per split hash item (256..32768, 12288),
+                                 halved per log2 step the table is below LOGCAP,
+                                 and halved in the per-source calls            */
   LP_OPT_SPLIT_LOGCAP = 5,    /* log2 slots of a split hash item (6..14, 14)     */
   LP_OPT_MED_MAX_WEDGES = 6,  /* medium tier: W <= this (1..1024, 1024); the
                                  warp tier takes precedence                     */

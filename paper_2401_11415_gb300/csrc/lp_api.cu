@@ -187,7 +187,7 @@ lp_status lp_set_option(lp_option option, int64_t value) {
       lp::g_opt.cta_max = (int)value;
       return LP_OK;
     case LP_OPT_SPLIT_TARGET:
-      if (value < 256 || value > 12288) break;
+      if (value < 256 || value > 32768) break;
       lp::g_opt.split_target = (int)value;
       return LP_OK;
     case LP_OPT_SPLIT_LOGCAP:
@@ -468,8 +468,9 @@ ScanArgs base_args_opts(Graph& g, int measure, int cap, double threshold, int mo
   A.cta_max = std::max(A.med_max, std::min(o.cta_max, 1 << (big_logcap - 1)));
   A.item_wedges = (int)o.item_wedges;
   A.split_logcap = std::min(o.split_logcap, big_logcap);
-  // a smaller split table than asked for takes proportionally fewer wedges
-  A.split_target = std::max(256, o.split_target >> (o.split_logcap - A.split_logcap));
+  // a smaller split table than asked for takes proportionally fewer wedges;
+  // per-source items also keep k-best lists beside the table: half as many
+  A.split_target = std::max(256, o.split_target >> (o.split_logcap - A.split_logcap + mode));
   A.off = g.d_off;
   A.idx = g.d_idx;
   A.deg = g.d_deg;

@@ -26,7 +26,7 @@ constexpr int kCtaThreads = 1024;        // large tier: one 32-warp CTA per item
 constexpr int kCtaWarps = kCtaThreads / 32;
 constexpr int kCtaSlots = 16384;         // largest CTA hash table
 constexpr int kCtaMaxWedges = 8192;      // single-item hash: W <= this
-constexpr int kSplitTarget = 6144;       // wedges per split hash item
+constexpr int kSplitTarget = 12288;      // wedges per split hash item
 constexpr int kCtaSmem = 192 * 1024;     // table bytes of a 1024-thread large-tier CTA
 // shared memory of a large-tier CTA of `threads` threads beyond its table:
 // 3 * threads window boundaries (or arc cursors) and a queue of `threads`

@@ -260,7 +260,13 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
         const u64 sh = (W + A.split_target - 1) / A.split_target;
         const u64 sd = (span + bspan - 1) / bspan;
         const u64 pdi = max((u64)1, min(sd, (W + A.item_wedges - 1) / A.item_wedges));
-        const double cost_h = (double)sh * (kept * 24.0 + (1 << A.split_logcap) / 4.0) + W * 3.0;
+        // relative costs (measured on R-MAT sweeps): a dense window is
+        // scanned whole, a split hash item re-reads every arc; in the global
+        // mode a dense 64-bit window holds an eighth of the ids of an 8-bit
+        // one, which tips AA / RA further towards hash items
+        const double hw = (MODE == 0 && V64) ? 0.6 : 1.0;
+        const double cost_h =
+            hw * ((double)sh * (kept * 24.0 + (1 << A.split_logcap) / 4.0) + W * 3.0);
         const double cost_d =
             (double)sd * (kept * 2.0 + bspan / 8.0) + (double)W + (double)pdi * kept * 24.0;
         logcap = A.split_logcap;

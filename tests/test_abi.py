@@ -45,9 +45,10 @@ def test_version_and_options(lp):
     assert "sm_103a" in lp.lp_version()
     assert lp.lp_get_option(lp.LP_OPT_WARP_MAX_WEDGES) == 256
     assert lp.lp_get_option(lp.LP_OPT_MED_MAX_WEDGES) == 1024
+    old = lp.lp_get_option(lp.LP_OPT_SPLIT_TARGET)
     lp.lp_set_option(lp.LP_OPT_SPLIT_TARGET, 4096)
     assert lp.lp_get_option(lp.LP_OPT_SPLIT_TARGET) == 4096
-    lp.lp_set_option(lp.LP_OPT_SPLIT_TARGET, 6144)
+    lp.lp_set_option(lp.LP_OPT_SPLIT_TARGET, old)
     with pytest.raises(lp.LPError) as e:
         lp.lp_set_option(lp.LP_OPT_WARP_MAX_WEDGES, 100000)
     assert e.value.status == lp.LP_EINVAL
