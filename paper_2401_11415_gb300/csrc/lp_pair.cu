@@ -4,11 +4,11 @@
 // count |Gamma_u ∩ Gamma_v| over intermediaries b with |Gamma_b| <= L_H that
 // every predicted link reports (Section 4.1.5) is recomputed for the links the
 // selection kept.  Their top pairs join high-degree vertices, and a vertex
-// takes part in many of them, so the links are grouped by u: one CTA marks
-// Gamma_u (hub test applied) in a shared-memory bitmap over all vertices, and
-// its warps count, for every link (u, v) of the group, the marked entries of
-// Gamma_v.  Building the groups is a counting sort by u (histogram, scan,
-// scatter) in a handful of small kernels.
+// takes part in many of them, so the links are grouped by their endpoint of
+// larger degree, u: one CTA marks Gamma_u (hub test applied) in a shared-memory
+// bitmap over all vertices, and its warps count, for every link (u, v) of the
+// group, the marked entries of the shorter Gamma_v.  Building the groups is a
+// counting sort by u (histogram, scan, scatter) in a handful of small kernels.
 #include "lp_internal.cuh"
 
 namespace lp {
@@ -18,9 +18,17 @@ namespace lp {
 constexpr int kScanThreads = 1024;
 constexpr int kScanChunk = kScanThreads * 4;  // int2 entries per block
 
-__global__ void k_pair_hist(const lp_link* __restrict__ links, u64 n, int* __restrict__ cnt) {
+// A link is grouped under its endpoint of larger degree (u on a tie), so
+// the list streamed per link is the shorter one.
+__device__ __forceinline__ int pair_owner(const lp_link& L, const int* __restrict__ off) {
+  const int du = off[L.u + 1] - off[L.u], dv = off[L.v + 1] - off[L.v];
+  return du >= dv ? L.u : L.v;
+}
+
+__global__ void k_pair_hist(const lp_link* __restrict__ links, u64 n, const int* __restrict__ off,
+                            int* __restrict__ cnt) {
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
-    atomicAdd(&cnt[links[i].u], 1);
+    atomicAdd(&cnt[pair_owner(links[i], off)], 1);
 }
 
 // Exclusive scan of the pairs v[i] (i < n) of one chunk of kScanChunk entries
@@ -117,10 +125,11 @@ __global__ void k_pair_groups(const int* __restrict__ cnt, const int2* __restric
 
 // perm: link indices grouped by u (the group starts in sc[u].x serve as
 // cursors; the groups were recorded before).
-__global__ void k_pair_scatter(const lp_link* __restrict__ links, u64 n, int2* __restrict__ sc,
+__global__ void k_pair_scatter(const lp_link* __restrict__ links, u64 n,
+                               const int* __restrict__ off, int2* __restrict__ sc,
                                int* __restrict__ perm) {
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
-    perm[atomicAdd(&sc[links[i].u].x, 1)] = (int)i;
+    perm[atomicAdd(&sc[pair_owner(links[i], off)].x, 1)] = (int)i;
 }
 
 // One group at a time per CTA (claimed from *claim): mark Gamma_u (b with
@@ -154,7 +163,8 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
     __syncthreads();
     for (int j = wid; j < G.z; j += blockDim.x >> 5) {  // warp-uniform trips
       const int li = perm[G.y + j];
-      const int v = links[li].v;
+      const lp_link L = links[li];
+      const int v = L.u == u ? L.v : L.u;
       int c = 0;
       const int ee = off[v + 1];
       int e = off[v] + lane;
@@ -194,7 +204,7 @@ size_t pair_groups_scratch(int n, u64 nlinks) {
          align256(((n1 + kScanChunk - 1) / kScanChunk) * sizeof(int2)) + 256;
 }
 
-// Counts of links[0, n) grouped by u; scratch of pair_groups_scratch bytes.
+// Counts of links[0, n), grouped by the endpoint of larger degree; scratch of pair_groups_scratch bytes.
 cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off, const int* idx,
                                   const Arc* arc, int cap, void* scratch, cudaStream_t st,
                                   int* launches) {
@@ -217,12 +227,12 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
   if (e == cudaSuccess) e = cudaMemsetAsync(claim, 0, sizeof(u32), st);
   if (e != cudaSuccess) return e;
   const int gb = (int)std::min<u64>((n + 255) / 256, 152 * 8);
-  k_pair_hist<<<gb, 256, 0, st>>>(links, n, cnt);
+  k_pair_hist<<<gb, 256, 0, st>>>(links, n, off, cnt);
   k_scan_counts<<<nb, kScanThreads, 0, st>>>(cnt, n1, sc, sums);
   k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, nb);
   k_scan_add<<<(n1 + 255) / 256, 256, 0, st>>>(sc, n1, sums);
   k_pair_groups<<<(nv + 255) / 256, 256, 0, st>>>(cnt, sc, nv, groups);
-  k_pair_scatter<<<gb, 256, 0, st>>>(links, n, sc, perm);
+  k_pair_scatter<<<gb, 256, 0, st>>>(links, n, off, sc, perm);
   const int nwords = (nv + 31) / 32;
   const size_t smem = (size_t)nwords * 4;
   e = cudaFuncSetAttribute(k_pair_cn_groups, cudaFuncAttributeMaxDynamicSharedMemorySize,
