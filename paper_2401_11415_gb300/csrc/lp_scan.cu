@@ -182,7 +182,32 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
       u64 Wj = 0;
       u32 kj = 0;
       int lj = INT_MAX, hj = -1;
-      for (int e = j0 + lane; e < j1; e += 32) {
+      // four arcs per lane at a time, so that a hub's walk keeps eight
+      // independent list reads in flight instead of two dependent ones
+      int e = j0 + lane;
+      for (; e + 96 < j1; e += 128) {
+        Arc t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u] = A.arc[e + 32 * u];
+        int l4[4], h4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int s0 = MODE ? t[u].y - t[u].z : t[u].x + 1;
+          const bool use = t[u].z <= A.cap && s0 < t[u].y;
+          l4[u] = use ? __ldg(A.idx + s0) : INT_MAX;
+          h4[u] = use ? __ldg(A.idx + t[u].y - 1) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (t[u].z <= A.cap) {
+            Wj += MODE ? (u64)(t[u].z - 1) : (u64)(t[u].y - t[u].x - 1);
+            ++kj;
+          }
+          lj = min(lj, l4[u]);
+          hj = max(hj, h4[u]);
+        }
+      }
+      for (; e < j1; e += 32) {
         const Arc t = A.arc[e];
         if (t.z <= A.cap) {
           Wj += MODE ? (u64)(t.z - 1) : (u64)(t.y - t.x - 1);
