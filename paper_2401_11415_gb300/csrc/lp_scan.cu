@@ -991,6 +991,11 @@ __device__ __forceinline__ bool score_dense8_linear(const ScanArgs& A, const Thr
   return fail;
 }
 
+// Mark of a first-order neighbour in the high word of a 64-bit counter pair:
+// added (not stored) during the insert phase, so its order against the
+// inserts does not matter.
+constexpr u32 kFirstOrder64 = 0x80000000u;
+
 // The same for 64-bit counters kept as two arrays of 32-bit halves (position
 // p: low word lo[p], high word hi[p]), so the low-word atomics of the scan
 // spread over all banks.
@@ -1008,19 +1013,24 @@ __device__ __forceinline__ bool score_dense64_linear(const ScanArgs& A, const Th
       *reinterpret_cast<uint4*>(hi + base) = make_uint4(0, 0, 0, 0);
     }
   }
+  // a first-order neighbour carries the mark kFirstOrder64 in its high word
+  // (real sums stay below 2^63); it is neither a candidate nor scored
+  const u32 hw[4] = {h4.x, h4.y, h4.z, h4.w};
   const u64 v4[4] = {(u64)l4.x | ((u64)h4.x << 32), (u64)l4.y | ((u64)h4.y << 32),
                      (u64)l4.z | ((u64)h4.z << 32), (u64)l4.w | ((u64)h4.w << 32)};
+  const u64 vm = max(vmin, (u64)1);
   bool any = false;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    n_cand += v4[j] != 0 ? 1 : 0;
-    any |= v4[j] != 0 && v4[j] >= vmin;
+    const bool first = (hw[j] & kFirstOrder64) != 0;
+    n_cand += v4[j] != 0 && !first ? 1 : 0;
+    any |= !first && v4[j] >= vm;
   }
   if (!__any_sync(FULLMASK, any)) return false;
   bool fail = false;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const bool live = v4[j] != 0 && v4[j] >= vmin;
+    const bool live = (hw[j] & kFirstOrder64) == 0 && v4[j] >= vm;
     fail |= survivors_push<u64>(A, T, a, da, live, lg + swz(base + j), v4[j], qn, qc, qv, qd);
   }
   return fail;
@@ -1655,12 +1665,18 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
       // (concatenated across the lanes), longer ones are queued for phase B.
       // With at most one arc per thread all but the shortest are queued.
       const int long_seg = K <= THREADS ? kShortSeg : kLongSeg;
+      // global-mode 64-bit dense windows mark the first-order neighbours in
+      // this pass (every arc of the source comes by) instead of a clearing
+      // pass after the inserts
+      const bool mark_first = MODE == 0 && V64 && is_dense;
       for (int eb = 0; eb < K; eb += THREADS) {  // CTA-uniform trips
         const int j = eb + lane * NW + wid;
         int st = 0, len = 0;
         V w = 0;
         if (j < K) {
           const Arc t = A.arc[e0 + j];
+          if (mark_first && t.w >= lg && t.w < hg && t.w > a)
+            atomicAdd(dhi + swz(t.w - lg), kFirstOrder64);
           if (t.z <= A.cap) {
             int s0 = MODE ? t.y - t.z : t.x + 1, s1 = t.y;
             if (s0 < s1) {
@@ -1760,7 +1776,9 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
         __syncthreads();
         break;  // hash items have a single range
       }
-      // drop first-order neighbours inside [lg, hg)
+      // drop first-order neighbours inside [lg, hg) (marked above in the
+      // global-mode 64-bit dense windows; the last phase ended with a barrier)
+      if (!(MODE == 0 && V64 && is_dense)) {
       for (int e = e0 + threadIdx.x; e < e1; e += THREADS) {
         const int b = __ldg(A.idx + e);
         if (b < lg || b >= hg || (MODE == 0 && b <= a)) continue;
@@ -1770,16 +1788,13 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
         } else if (is_dense && d16) {
           const int p = swz(b - lg);
           atomicAnd(reinterpret_cast<u32*>(dense) + (p >> 1), ~(0xffffu << ((p & 1) << 4)));
-        } else if (is_dense && MODE == 0 && V64) {
-          const int p = swz(b - lg);
-          dlo[p] = 0;
-          dhi[p] = 0;
         } else if (is_dense) {
           dense[swz(b - lg)] = 0;
         }
         else hash_kill<V>(keys, vals, logcap, b);
       }
       __syncthreads();
+      }
       // score and select.  Global mode: every counter or slot once, the ones
       // below the count floor only counted.  Per-source mode: the touched
       // counters (dense) or the packed live slots (hash).
