@@ -490,9 +490,19 @@ ScanArgs base_args_opts(Graph& g, int measure, int cap, double threshold, int mo
 
 // Split an overflowed hash item into two halves (dense when narrow enough).
 static void split_item(const int4& r, int dense_span, std::vector<int4>& out) {
-  const int lo = r.y, hi = r.z;
+  int lo = r.y;
+  const int hi = r.z;
   const int logcap = (r.w >> 8) & 0xff;
   const int keep = r.w & kItemSingle;
+  const int G = ((r.w >> 16) & 0xfff) + 1;
+  if (G > 1) {
+    // a sweep that overflowed in its first remaining range: that range is
+    // split below, the ranges after it stay one sweep
+    const int first_end = lo + (int)(((long long)(hi - lo)) / G);
+    out.push_back(make_int4(r.x, first_end, hi, (logcap << 8) | ((G - 2) << 16)));
+    split_item(make_int4(r.x, lo, first_end, logcap << 8), dense_span, out);
+    return;
+  }
   if (hi - lo <= dense_span) {
     out.push_back(make_int4(r.x, lo, hi, kItemDense | (logcap << 8)));
     return;

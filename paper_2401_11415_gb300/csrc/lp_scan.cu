@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
     }
     // large tier: P items per source
     int P = 0, kind = 0, logcap = 0, Gd = 1, bspan = A.big_span;
+    u64 nsub = 1;  // hash items: sub-ranges of the source
     if (tier == 2) {
       const u64 span = (u64)(hi - lo);
       if (W <= (u64)A.cta_max) {
@@ -300,7 +301,14 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
           P = (int)((sd + Gd - 1) / Gd);
           kind = kItemDense | (d8 ? kItemD8 : 0);
         } else {
-          P = (int)min(sh, span);
+          // sub-ranges of about split_target wedges; in the global mode an
+          // item sweeps Gd consecutive ones (per-arc cursors carried from
+          // range to range), items of about item_wedges wedges
+          const u64 ps = min(sh, span);
+          const u64 ph = MODE == 0 ? max((u64)1, min(ps, (W + A.item_wedges - 1) / A.item_wedges)) : ps;
+          Gd = (int)((ps + ph - 1) / ph);
+          P = (int)((ps + Gd - 1) / Gd);
+          nsub = ps;
         }
       }
       if (MODE && P == 1) kind |= kItemSingle;
@@ -330,8 +338,10 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
             h2 = lo + (int)min(span, (u64)(p + 1) * Gd * bspan);
             gcount = (h2 - l2 + bspan - 1) / bspan;
           } else {
-            l2 = lo + (int)((span * (u64)p) / (u64)P);
-            h2 = lo + (int)((span * (u64)(p + 1)) / (u64)P);
+            const u64 s0 = (u64)p * Gd, s1 = min(nsub, (u64)(p + 1) * Gd);
+            l2 = lo + (int)((span * s0) / nsub);
+            h2 = lo + (int)((span * s1) / nsub);
+            gcount = (int)(s1 - s0);
           }
           itemq[first + p] = make_int4(r, l2, h2, kind | (logcap << 8) | ((gcount - 1) << 16));
         }
@@ -1583,7 +1593,8 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
     const bool is_dense = (rec.w & kItemDense) != 0;
     const bool d8 = d16 && (rec.w & kItemD8) != 0;  // 8-bit counters for this item
     const int logcap = (rec.w >> 8) & 0xff;
-    const int G = is_dense ? ((rec.w >> 16) & 0xfff) + 1 : 1;
+    // dense items sweep G windows; global-mode hash items G ranges
+    const int G = (is_dense || MODE == 0) ? ((rec.w >> 16) & 0xfff) + 1 : 1;
     const int nslots = 1 << logcap;
     const int limit = (nslots * 3) / 4;
     const int span = hi - lo;
@@ -1611,6 +1622,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
     int tcnt = 0;
     bool fail = false;
     bool overflowed = false;
+    int g_over = 0;  // the range that overflowed (ranges before it are done)
     for (int g = 0; g < G; ++g) {
       const int lg = lo + (int)(((u64)span * (u64)g) / (u64)G);
       const int hg = lo + (int)(((u64)span * (u64)(g + 1)) / (u64)G);
@@ -1773,8 +1785,9 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
           zero4<V>(vals + i);
         }
         overflowed = true;
+        g_over = g;
         __syncthreads();
-        break;  // hash items have a single range
+        break;  // the rest of the item goes back for splitting
       }
       // drop first-order neighbours inside [lg, hg) (marked above in the
       // global-mode 64-bit dense windows; the last phase ended with a barrier)
@@ -1848,8 +1861,12 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
     }
     if (overflowed) {
       if (threadIdx.x == 0) {
+        // hand back [start of the overflowed range, hi) with its G - g_over ranges
+        int4 back = rec;
+        back.y = lo + (int)(((u64)span * (u64)g_over) / (u64)G);
+        back.w = (rec.w & 0xffff) | ((G - g_over - 1) << 16);
         const u64 f = atomicAdd(&A.ctr->nsplit, 1ull);
-        if (f < A.split_cap) A.split[f] = rec;
+        if (f < A.split_cap) A.split[f] = back;
         else A.ctr->error = 2u;
       }
       __syncthreads();
