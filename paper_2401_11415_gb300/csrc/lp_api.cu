@@ -788,18 +788,11 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
     CU(launch_emit_global(res, nwrite, measure, g.fixbits, d_links, st));
     t_stats.launches++;
     if (measure == LP_AA || measure == LP_RA) {
-      // grouped by the endpoint of larger degree (the top pairs share
-      // high-degree endpoints) while a bitmap over the vertices fits in
-      // shared memory; per-link lookups otherwise
-      if (pair_groups_fit(g.n)) {
-        CU(ensure(g, g.s_pair, pair_groups_scratch(g.n, nwrite)));
-        CU(launch_pair_cn_groups(d_links, nwrite, g.n, g.d_off, g.d_idx, g.d_arc, A.cap,
-                                 g.s_pair.p, st, &t_stats.launches));
-      } else {
-        CU(launch_pair_cn(d_links, nullptr, 1, nwrite, g.d_off, g.d_idx, g.d_deg, g.d_arc, A.cap,
-                          st));
-        t_stats.launches++;
-      }
+      // grouped by the endpoint of larger degree: the top pairs share
+      // high-degree endpoints, whose lists are then read once per group
+      CU(ensure(g, g.s_pair, pair_groups_scratch(g.n, nwrite)));
+      CU(launch_pair_cn_groups(d_links, nwrite, g.n, g.d_off, g.d_idx, g.d_arc, A.cap, g.s_pair.p,
+                               st, &t_stats.launches));
     }
     if (!out_dev)
       CU(cudaMemcpyAsync(out, d_links, sizeof(lp_link) * nwrite, cudaMemcpyDeviceToHost, st));

@@ -226,10 +226,9 @@ cudaError_t launch_emit_global(const Cand* c, u64 n, int measure, int fixbits, l
                                cudaStream_t st);
 cudaError_t launch_emit_sources(const TopEnt* top, const int* cnt, const int* sources, int n_src,
                                 int k, int measure, int fixbits, lp_link* out, cudaStream_t st);
-// Common-neighbour counts of global-mode links grouped by u (lp_pair.cu):
-// needs the graph's n to fit the shared-memory bitmap (pair_groups_fit) and
-// pair_groups_scratch(n, links) bytes of device scratch.
-bool pair_groups_fit(int n);
+// Common-neighbour counts of global-mode links grouped by their endpoint of
+// larger degree (lp_pair.cu); pair_groups_scratch(n, links) bytes of device
+// scratch.
 size_t pair_groups_scratch(int n, u64 nlinks);
 cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off, const int* idx,
                                   const Arc* arc, int cap, void* scratch, cudaStream_t st,

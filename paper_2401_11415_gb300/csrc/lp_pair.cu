@@ -5,10 +5,12 @@
 // every predicted link reports (Section 4.1.5) is recomputed for the links the
 // selection kept.  Their top pairs join high-degree vertices, and a vertex
 // takes part in many of them, so the links are grouped by their endpoint of
-// larger degree, u: one CTA marks Gamma_u (hub test applied) in a shared-memory
-// bitmap over all vertices, and its warps count, for every link (u, v) of the
-// group, the marked entries of the shorter Gamma_v.  Building the groups is a
-// counting sort by u (histogram, scan, scatter) in a handful of small kernels.
+// larger degree, u: one CTA marks Gamma_u (hub test applied) in shared memory
+// (a bitmap over the vertex ids, in windows of ids when they do not all fit,
+// or a hash set when Gamma_u is short and the ids need several windows), and
+// its warps count, for every link (u, v) of the group, the marked entries of
+// the shorter Gamma_v.  Building the groups is a counting sort by u
+// (histogram, scan, scatter) in a handful of small kernels.
 #include "lp_internal.cuh"
 
 namespace lp {
@@ -94,16 +96,31 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_counts(const int* __restr
   if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-// Exclusive scan of the nb <= kScanChunk chunk totals, in place (one block).
+// Exclusive scan of the nb chunk totals, in place (one block, kScanChunk at a
+// time with a running carry).
 __global__ void __launch_bounds__(kScanThreads) k_scan_sums(int2* __restrict__ sums, int nb) {
-  int2 v[4];
+  int2 carry = make_int2(0, 0);
+  for (int base = 0; base < nb; base += kScanChunk) {  // block-uniform trips
+    int2 v[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int i = threadIdx.x * 4 + j;
-    v[j] = i < nb ? sums[i] : make_int2(0, 0);
+    for (int j = 0; j < 4; ++j) {
+      const int i = base + threadIdx.x * 4 + j;
+      v[j] = i < nb ? sums[i] : make_int2(0, 0);
+    }
+    __syncthreads();  // every value read before any is overwritten
+    const int2 tot = scan_chunk(v, base, nb, sums);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {  // the entries this thread wrote
+      const int i = base + threadIdx.x * 4 + j;
+      if (i < nb) {
+        sums[i].x += carry.x;
+        sums[i].y += carry.y;
+      }
+    }
+    carry.x += tot.x;
+    carry.y += tot.y;
+    __syncthreads();  // scan_chunk's staging is reused by the next chunk
   }
-  __syncthreads();  // every value read before any is overwritten
-  scan_chunk(v, 0, nb, sums);
 }
 
 __global__ void k_scan_add(int2* __restrict__ sc, int n, const int2* __restrict__ sums) {
@@ -132,10 +149,29 @@ __global__ void k_pair_scatter(const lp_link* __restrict__ links, u64 n,
     perm[atomicAdd(&sc[pair_owner(links[i], off)].x, 1)] = (int)i;
 }
 
-// One group at a time per CTA (claimed from *claim): mark Gamma_u (b with
-// |Gamma_b| <= cap) in the bitmap, count the marks in Gamma_v for every link
-// of the group (a warp per link), then clear the marks.  *ngroups is the
-// total the scan left after the last vertex.
+// Position of the first entry >= key in the sorted idx[lo, hi).
+__device__ __forceinline__ int pair_lower_bound(const int* __restrict__ idx, int lo, int hi, int key) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(idx + mid) < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kPairHashLog = 14;                    // hash-set slots (64 KB of keys)
+constexpr int kPairHashMaxDeg = 1 << (kPairHashLog - 1);
+
+__device__ __forceinline__ u32 pair_hash(int b) {
+  return ((u32)b * 0x9E3779B1u) >> (32 - kPairHashLog);
+}
+
+// One group at a time per CTA (claimed from *claim): the marked set is Gamma_u
+// (b with |Gamma_b| <= cap); every link (u, v) of the group counts the marked
+// entries of Gamma_v (a warp per link).  The set is a bitmap over the ids
+// [w0, w0 + 32 * nwords): over all vertices when they fit, else one window of
+// ids at a time; a group whose Gamma_u is short uses a hash set of its
+// entries (keys b + 1, 0 = empty) in the same shared memory instead.
+// *ngroups is the total the scan left after the last vertex.
 __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict__ links,
                                                             const int* __restrict__ perm,
                                                             const int4* __restrict__ groups,
@@ -143,11 +179,14 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
                                                             const int* __restrict__ off,
                                                             const int* __restrict__ idx,
                                                             const Arc* __restrict__ arc, int cap,
-                                                            int nwords, u32* __restrict__ claim) {
+                                                            int nwords, int n,
+                                                            u32* __restrict__ claim) {
   extern __shared__ u32 bits[];
   __shared__ u32 s_g;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const u32 ngroups = (u32)total->y;
+  const int width = nwords * 32;
+  const bool one_window = n <= width;
   for (int i = threadIdx.x; i < nwords; i += blockDim.x) bits[i] = 0;
   for (;;) {
     if (threadIdx.x == 0) s_g = atomicAdd(claim, 1u);
@@ -156,40 +195,78 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
     if (gi >= ngroups) break;
     const int4 G = groups[gi];
     const int u = G.x, e0 = off[u], e1 = off[u + 1];
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const Arc t = arc[e];  // b = t.w, |Gamma_b| = t.z
-      if (t.z <= cap) atomicOr(&bits[t.w >> 5], 1u << (t.w & 31));
-    }
-    __syncthreads();
-    for (int j = wid; j < G.z; j += blockDim.x >> 5) {  // warp-uniform trips
-      const int li = perm[G.y + j];
-      const lp_link L = links[li];
-      const int v = L.u == u ? L.v : L.u;
-      int c = 0;
-      const int ee = off[v + 1];
-      int e = off[v] + lane;
-      for (; e + 96 < ee; e += 128) {  // four loads in flight per lane
-        const int b0 = __ldg(idx + e), b1 = __ldg(idx + e + 32), b2 = __ldg(idx + e + 64),
-                  b3 = __ldg(idx + e + 96);
-        c += ((bits[b0 >> 5] >> (b0 & 31)) & 1u) + ((bits[b1 >> 5] >> (b1 & 31)) & 1u) +
-             ((bits[b2 >> 5] >> (b2 & 31)) & 1u) + ((bits[b3 >> 5] >> (b3 & 31)) & 1u);
+    if (!one_window && e1 - e0 <= kPairHashMaxDeg) {
+      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const Arc t = arc[e];  // b = t.w, |Gamma_b| = t.z
+        if (t.z > cap) continue;
+        u32 h = pair_hash(t.w);
+        while (atomicCAS(&bits[h], 0u, (u32)t.w + 1u) != 0u)  // keys are distinct
+          h = (h + 1) & ((1u << kPairHashLog) - 1);
       }
-      for (; e < ee; e += 32) {
+      __syncthreads();
+      for (int j = wid; j < G.z; j += nw) {  // warp-uniform trips
+        const int li = perm[G.y + j];
+        const lp_link L = links[li];
+        const int v = L.u == u ? L.v : L.u;
+        int c = 0;
+        for (int e = off[v] + lane; e < off[v + 1]; e += 32) {
+          const u32 key = (u32)__ldg(idx + e) + 1u;
+          u32 h = pair_hash((int)key - 1);
+          for (;;) {  // at most half the slots are taken, so an empty one comes
+            const u32 k2 = bits[h];
+            if (k2 == key) { ++c; break; }
+            if (k2 == 0u) break;
+            h = (h + 1) & ((1u << kPairHashLog) - 1);
+          }
+        }
+        c = __reduce_add_sync(FULLMASK, (u32)c);
+        if (lane == 0) links[li].cn = c;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < (1 << kPairHashLog); i += blockDim.x) bits[i] = 0;
+      __syncthreads();
+      continue;
+    }
+    for (int w0 = 0; w0 < n; w0 += width) {  // one pass when the bitmap covers every id
+      const int w1 = min(n, w0 + width);
+      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const int b = __ldg(idx + e);
-        c += (bits[b >> 5] >> (b & 31)) & 1u;
+        if (b < w0 || b >= w1) continue;
+        if (arc[e].z <= cap) atomicOr(&bits[(b - w0) >> 5], 1u << ((b - w0) & 31));
       }
-      c = __reduce_add_sync(FULLMASK, (u32)c);
-      if (lane == 0) links[li].cn = c;
+      __syncthreads();
+      for (int j = wid; j < G.z; j += nw) {  // warp-uniform trips
+        const int li = perm[G.y + j];
+        const lp_link L = links[li];
+        const int v = L.u == u ? L.v : L.u;
+        int c = 0;
+        const int vs = off[v], ve = off[v + 1];
+        const int ee = one_window ? ve : pair_lower_bound(idx, vs, ve, w1);
+        int e = (one_window ? vs : pair_lower_bound(idx, vs, ve, w0)) + lane;
+        for (; e + 96 < ee; e += 128) {  // four loads in flight per lane
+          const int b0 = __ldg(idx + e) - w0, b1 = __ldg(idx + e + 32) - w0,
+                    b2 = __ldg(idx + e + 64) - w0, b3 = __ldg(idx + e + 96) - w0;
+          c += ((bits[b0 >> 5] >> (b0 & 31)) & 1u) + ((bits[b1 >> 5] >> (b1 & 31)) & 1u) +
+               ((bits[b2 >> 5] >> (b2 & 31)) & 1u) + ((bits[b3 >> 5] >> (b3 & 31)) & 1u);
+        }
+        for (; e < ee; e += 32) {
+          const int b = __ldg(idx + e) - w0;
+          c += (bits[b >> 5] >> (b & 31)) & 1u;
+        }
+        c = __reduce_add_sync(FULLMASK, (u32)c);
+        if (lane == 0) {
+          if (w0 == 0) links[li].cn = c;
+          else links[li].cn += c;
+        }
+      }
+      __syncthreads();
+      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int b = __ldg(idx + e);
+        if (b >= w0 && b < w1) bits[(b - w0) >> 5] = 0;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) bits[__ldg(idx + e) >> 5] = 0;
-    __syncthreads();
   }
-}
-
-bool pair_groups_fit(int n) {
-  return n > 0 && (size_t)(n + 31) / 32 * 4 <= 224 * 1024 && (long long)n + 1 <=
-         (long long)kScanChunk * kScanChunk;
 }
 
 // Scratch layout: sc int2[n + 1], cnt int[n + 1], perm int[links], groups
@@ -233,7 +310,9 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
   k_scan_add<<<(n1 + 255) / 256, 256, 0, st>>>(sc, n1, sums);
   k_pair_groups<<<(nv + 255) / 256, 256, 0, st>>>(cnt, sc, nv, groups);
   k_pair_scatter<<<gb, 256, 0, st>>>(links, n, off, sc, perm);
-  const int nwords = (nv + 31) / 32;
+  // a bitmap over every vertex when it fits in 224 KB, else windows of that
+  // size (and room for the hash set)
+  const int nwords = std::max(1 << kPairHashLog, std::min((nv + 31) / 32, 224 * 1024 / 4));
   const size_t smem = (size_t)nwords * 4;
   e = cudaFuncSetAttribute(k_pair_cn_groups, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            224 * 1024);
@@ -242,7 +321,7 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   k_pair_cn_groups<<<nsm, 1024, smem, st>>>(links, perm, groups, sc + nv, off, idx, arc, cap,
-                                            nwords, claim);
+                                            nwords, nv, claim);
   if (launches) *launches += 7;
   return cudaGetLastError();
 }

@@ -11,6 +11,9 @@ that the oracle computes one by one, and by properties that hold at any size.
   of every vertex for all nine measures at the paper's hub limits (4 for HP
   and LHN, 32 for CN and AA, 256 for the rest) and IBase for JC and RA on a
   source sample, sampled rows against the oracle.
+* Chung-Lu 4,194,304 vertices, global top-200,000 DLH(256) AA and RA:
+  sampled links' common-neighbour counts and scores against the oracle
+  (vertex ids in several bitmap windows).
 * R-MAT scale 24 (the serving graph): top-10 DLH(256) RA requests of 1, 300
   and 4096 sources, sampled rows against the oracle.
 """
@@ -159,6 +162,34 @@ def test_chunglu4m_per_source_all_vertices(lp, chunglu4m):
             _per_source_check(lp, G, g, m, None, sample, 10, 60, rng)
         st = lp.lp_last_stats()
         assert all(x > 0 for x in st["tier_launches"])  # every tier ran
+
+
+@pytest.mark.parametrize("measure", ["RA", "AA"])
+def test_chunglu4m_global_pair_counts(lp, chunglu4m, measure):
+    """Global AA/RA on a graph whose vertex ids do not fit one shared-memory
+    bitmap: the common-neighbour counts of the emitted links come from the
+    windowed bitmap (links owned by an endpoint of degree above 8192) or the
+    hash set (the others); sampled links of both kinds against the oracle."""
+    g = chunglu4m
+    k = 200000
+    with lp.Graph.from_csr(g) as G:
+        got = G.predict(measure, 256, k)
+    assert len(got) == k
+    deg = np.diff(g.off)
+    u = got["u"].astype(np.int64)
+    v = got["v"].astype(np.int64)
+    owner_deg = np.maximum(deg[u], deg[v])
+    rng = np.random.default_rng(31)
+    big = np.nonzero(owner_deg > 8192)[0]
+    small = np.nonzero(owner_deg <= 8192)[0]
+    assert len(big) > 0 and len(small) > 0
+    pick = np.concatenate([rng.choice(big, min(60, len(big)), replace=False),
+                           rng.choice(small, 60, replace=False)])
+    for i in pick.tolist():
+        r, adj = oracle.pair(g.n, g.off, g.idx, measure, int(u[i]), int(v[i]), 256)
+        assert not adj
+        assert int(got["cn"][i]) == int(r["cn"]), (measure, int(u[i]), int(v[i]))
+        assert abs(float(got["score"][i]) - float(r["value"])) <= TOL * float(r["value"])
 
 
 def test_grid_per_source_all_vertices(lp):
