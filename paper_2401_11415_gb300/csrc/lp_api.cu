@@ -125,7 +125,8 @@ static void free_graph(Graph* g) {
   Graph::Scratch* all[] = {&g->s_ctr, &g->s_w, &g->s_warpq, &g->s_itemq, &g->s_warpq2,
                            &g->s_itemq2, &g->s_medq, &g->s_medq2, &g->s_buf, &g->s_buf2,
                            &g->s_buf3, &g->s_misc, &g->s_failed, &g->s_split,
-                           &g->s_thresh, &g->s_vfloor, &g->s_pair, &g->s_flags, &g->s_partial,
+                           &g->s_thresh, &g->s_vfloor, &g->s_pair, &g->s_gcur, &g->s_flags,
+                           &g->s_partial,
                            &g->s_phdr, &g->s_top,
                            &g->s_cnt, &g->s_links, &g->s_src, &g->s_grp};
   for (auto* s : all)
@@ -429,6 +430,21 @@ static void estimate_stats(const Counters& h) {
   }
 }
 
+cudaError_t attach_cursors(Graph& g, ScanArgs& A) {
+  int dev = 0, nsm = 1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int ctas = 2 * nsm;  // the large tier runs at most two CTAs per SM
+  const size_t stride = (size_t)g.dmax + 1;
+  e = ensure(g, g.s_gcur, sizeof(int) * stride * (size_t)ctas);
+  if (e != cudaSuccess) return e;
+  A.gcur = sp<int>(g.s_gcur);
+  A.gcur_stride = (int)stride;
+  A.gcur_ctas = ctas;
+  return cudaSuccess;
+}
+
 static ScanArgs base_args(Graph& g, int measure, int cap, double threshold, int mode, int k) {
   return base_args_opts(g, measure, cap, threshold, mode, k, options_snapshot());
 }
@@ -637,6 +653,7 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
   tm.mark(0);
   ScanArgs A = base_args(g, measure, cap, threshold, 0, 0);
   A.rec_base = src_begin;
+  CU(attach_cursors(g, A));
   // selection buffer
   const u64 minbuf = (u64)std::max<long long>(16, options_snapshot().select_buffer);
   u64 C = k > 0 ? std::max<u64>(minbuf, 2ull * (u64)k + std::min<u64>(minbuf, 1ull << 20)) : minbuf;
@@ -837,6 +854,7 @@ static lp_status predict_sources(Graph& g, int measure, int cap, const int* d_sr
   }
   ScanArgs A = base_args(g, measure, cap, threshold, 1, k);
   A.sources = d_src;
+  CU(attach_cursors(g, A));
   CU(ensure(g, g.s_top, sizeof(TopEnt) * (size_t)n_src * k));
   CU(ensure(g, g.s_grp, sizeof(int2) * ((size_t)n_src + 1)));
   CU(ensure(g, g.s_split, sizeof(int4) * (1 << 20)));

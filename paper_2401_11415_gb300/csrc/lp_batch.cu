@@ -82,6 +82,7 @@ lp_status build_plan(Graph& g, AllPlan& P, int measure, int cap, int k, const Op
   cudaStream_t st = g.stream;
   const int n = g.n;
   ScanArgs A = base_args_opts(g, measure, cap, 0.0, 1, k, opt);
+  BU(attach_cursors(g, A));
   A.no_split = P.dense_only ? 1 : 0;
   A.partial_by_item = 1;
   BU(ensure(g, P.src, sizeof(int) * ((size_t)n + 1)));

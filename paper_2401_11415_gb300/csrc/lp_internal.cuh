@@ -113,6 +113,10 @@ struct ScanArgs {
   u64 buf_cap;
   const Thresh* thresh;
   const u64* vfloor;   // [dmax + 1]: count floor of a source degree under *thresh
+  int* gcur;           // large tier: per-arc cursors of sweeps over sources with more arcs
+                       // than the shared boundary table (gcur_stride ints per CTA), or null
+  int gcur_stride;
+  int gcur_ctas;
   // failure / split records
   int4* failed;
   u64 failed_cap;
@@ -179,7 +183,7 @@ struct Graph {
   };
   Scratch s_ctr, s_w, s_warpq, s_itemq, s_warpq2, s_itemq2, s_medq, s_medq2, s_buf, s_buf2,
       s_failed, s_split, s_thresh, s_flags, s_partial, s_phdr, s_top, s_cnt, s_links, s_src, s_grp,
-      s_buf3, s_misc, s_vfloor, s_pair;
+      s_buf3, s_misc, s_vfloor, s_pair, s_gcur;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // per kernel
 };
@@ -253,6 +257,9 @@ void stats_estimate(const Counters& h);
 void stats_add(int64_t candidates, int32_t splits, int32_t launches);
 ScanArgs scan_args(Graph& g, int measure, int cap, double threshold, int mode, int k);
 // scan_args with explicit options instead of the process-wide ones
+// Give the large tier its per-arc cursor scratch (allocates; not for the
+// allocation-free path, which leaves A.gcur null).
+cudaError_t attach_cursors(Graph& g, ScanArgs& A);
 ScanArgs base_args_opts(Graph& g, int measure, int cap, double threshold, int mode, int k,
                         const Options& o);
 // Grow a scratch allocation to at least `bytes` (contents are not kept).

@@ -1605,6 +1605,10 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
     // arc carried from window to window
     const bool pre = G > 1 && (long long)K * (G + 1) <= NB;
     const bool use_cur = G > 1 && !pre && K <= NB;
+    // more arcs than the shared table holds: the cursors live in this CTA's
+    // slice of a device scratch array (same arc, same thread every window)
+    const bool use_gcur = G > 1 && K > NB && A.gcur != nullptr && (int)blockIdx.x < A.gcur_ctas;
+    int* gcur = use_gcur ? A.gcur + (size_t)blockIdx.x * (size_t)A.gcur_stride : nullptr;
     if (pre) {
       for (int q2 = threadIdx.x; q2 < K * (G + 1); q2 += THREADS) {
         const int j = q2 / (G + 1);
@@ -1696,10 +1700,13 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
                 s0 = bnd[j * (G + 1) + g];
                 s1 = bnd[j * (G + 1) + g + 1];
               } else if (!full_range) {
-                const int b0 = (use_cur && g > 0) ? bnd[j] : lower_bound_interp(A.idx, s0, s1, lg);
-                const int b1 = use_cur ? lower_bound_gallop(A.idx, b0, s1, hg)
-                                       : lower_bound_interp(A.idx, b0, s1, hg);
+                const int b0 = (use_cur && g > 0)    ? bnd[j]
+                               : (use_gcur && g > 0) ? gcur[j]
+                                                     : lower_bound_interp(A.idx, s0, s1, lg);
+                const int b1 = (use_cur || use_gcur) ? lower_bound_gallop(A.idx, b0, s1, hg)
+                                                     : lower_bound_interp(A.idx, b0, s1, hg);
                 if (use_cur) bnd[j] = b1;
+                if (use_gcur) gcur[j] = b1;
                 s0 = b0;
                 s1 = b1;
               }
