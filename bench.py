@@ -304,18 +304,20 @@ def cpu_baseline(split):
         r = oracle.predict(obs.n, obs.off, obs.idx, m, c, k=k, nthreads=cores)
         t += time.perf_counter() - t0
         tot += len(r)
-    c1, m1 = SAMPLE_CAPS[0]
-    t0 = time.perf_counter()
-    r1 = oracle.predict(obs.n, obs.off, obs.idx, m1, c1, k=k, nthreads=1)
-    t1 = time.perf_counter() - t0
+    t1 = 0.0
+    n1 = 0
+    for c, m in SAMPLE_CAPS:
+        t0 = time.perf_counter()
+        n1 += len(oracle.predict(obs.n, obs.off, obs.idx, m, c, k=k, nthreads=1))
+        t1 += time.perf_counter() - t0
     return {"value": round(tot / t, 1), "unit": "edges/s", "cores": cores,
             "kind": "oracle",
             "sample": "the DLH cap-16 JC and RA calls of the step, full graph "
                       f"({tot} predicted edges in {t:.1f} s); caps 64-inf left out to "
                       "bound the run",
-            "one_thread": {"value": round(len(r1) / t1, 1), "unit": "edges/s", "cores": 1,
-                           "sample": f"the DLH cap-16 {m1} call alone ({len(r1)} predicted "
-                                     f"edges in {t1:.1f} s)"}}
+            "one_thread": {"value": round(n1 / t1, 1), "unit": "edges/s", "cores": 1,
+                           "sample": f"the same calls on one thread ({n1} predicted edges in "
+                                     f"{t1:.1f} s)"}}
 
 
 # ------------------------------------------------------------ serving ----
