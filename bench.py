@@ -13,9 +13,9 @@ value: sum of |P| over the step / step time, graph resident on the device,
 e2e:   the same step through the host-buffer API: lp_graph_create from the
        host CSR (pinned), ten lp_predict calls into host buffers,
        lp_graph_destroy.
-roofline: the dominant scan kernel, algorithmic bytes (Section 8(d) of the
-       survey's accounting: Gamma_a ids, degree of each b, the b offset of
-       kept arcs, 4 bytes per scanned wedge) / its event-timed duration.
+roofline: the dominant scan kernel, algorithmic bytes (Gamma_a ids, degree of
+       each b, the b offset of kept arcs, 4 bytes per scanned wedge) / its
+       event-timed duration.
 
 --impl reference runs the CPU oracle (the only reference this method has)
 on a bounded sample of the same workload.
