@@ -437,8 +437,14 @@ cudaError_t attach_cursors(Graph& g, ScanArgs& A) {
   if (e != cudaSuccess) return e;
   const int ctas = 2 * nsm;  // the large tier runs at most two CTAs per SM
   const size_t stride = (size_t)g.dmax + 1;
-  e = ensure(g, g.s_gcur, sizeof(int) * stride * (size_t)ctas);
-  if (e != cudaSuccess) return e;
+  const size_t bytes = sizeof(int) * stride * (size_t)ctas;
+  // a graph with a vertex of enormous degree does without (the sweeps then
+  // search each range's boundaries), and so does a device without room
+  if (bytes > (size_t)4 << 30) return cudaSuccess;
+  if (ensure(g, g.s_gcur, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return cudaSuccess;
+  }
   A.gcur = sp<int>(g.s_gcur);
   A.gcur_stride = (int)stride;
   A.gcur_ctas = ctas;
