@@ -30,8 +30,10 @@
  *     score first, then smaller u, then smaller v (per-source: smaller v).
  *     The seven count measures are ordered by their exact rational value
  *     (Salton through CN^2 / (|Gamma_a| |Gamma_c|)); AA and RA by their
- *     fixed-point sums (each weight rounded to 2^-F, F >= 40, then summed
- *     exactly), which agree with FP64 sums to better than 1e-9 relative.
+ *     fixed-point sums (each weight rounded to 2^-F with
+ *     F = min(50, 62 - ceil(log2(dmax + 1))), then summed exactly), which
+ *     agree with FP64 sums to within |Gamma_b|max * 2^-(F+1) relative: below
+ *     1e-9 for dmax < 2^16 and below 1e-6 for dmax < 2^21.
  */
 #ifndef LP_H
 #define LP_H
