@@ -41,6 +41,7 @@ constexpr int kItemDense = 1;    // dense counters over [lo, hi)
 constexpr int kItemSingle = 2;   // the only item of its source (per-source mode)
 constexpr int kItemWhole = 4;    // one item covers the source's whole second-order id range
 constexpr int kItemD8 = 8;       // dense, 8-bit counters (global mode, source degree <= 255)
+constexpr int kMaxSweep = 4096;  // windows or ranges of one item (a 12-bit field of the record)
 
 // Arc table entry for arc e = (a -> b): x = position of a in Gamma_b
 // (absolute index into idx), y = off[b + 1], z = |Gamma_b|, w = b.

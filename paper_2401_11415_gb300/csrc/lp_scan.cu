@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
             (double)sd * (kept * 2.0 + bspan / 8.0) + (double)W + (double)pdi * kept * 24.0;
         logcap = A.split_logcap;
         if (cost_d < cost_h || A.no_split) {  // dense items never overflow
-          Gd = (int)((sd + pdi - 1) / pdi);
+          Gd = (int)min((sd + pdi - 1) / pdi, (u64)kMaxSweep);
           P = (int)((sd + Gd - 1) / Gd);
           kind = kItemDense | (d8 ? kItemD8 : 0);
         } else {
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
           // range to range), items of about item_wedges wedges
           const u64 ps = min(sh, span);
           const u64 ph = MODE == 0 ? max((u64)1, min(ps, (W + A.item_wedges - 1) / A.item_wedges)) : ps;
-          Gd = (int)((ps + ph - 1) / ph);
+          Gd = (int)min((ps + ph - 1) / ph, (u64)kMaxSweep);
           P = (int)((ps + Gd - 1) / Gd);
           nsub = ps;
         }
