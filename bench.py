@@ -543,7 +543,8 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(t * 1e3 / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": sample},
+            "config": {"workload": WORKLOAD + (f" [subset: scale {args.scale}]"
+                                               if args.scale != 20 else ""), "sample": sample},
             "cpu_baseline": {"value": round(value, 1), "unit": "edges/s",
                              "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 1), "unit": "edges/s", "h2d_bytes_per_step": 0,
