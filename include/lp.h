@@ -32,8 +32,12 @@
  *     (Salton through CN^2 / (|Gamma_a| |Gamma_c|)); AA and RA by their
  *     fixed-point sums (each weight rounded to 2^-F with
  *     F = min(50, 62 - ceil(log2(dmax + 1))), then summed exactly), which
- *     agree with FP64 sums to within |Gamma_b|max * 2^-(F+1) relative: below
- *     1e-9 for dmax < 2^16 and below 1e-6 for dmax < 2^21.
+ *     agree with FP64 sums to within |Gamma_b|max * 2^-(F+1) relative for RA
+ *     and ln|Gamma_b|max * 2^-(F+1) for AA, |Gamma_b|max = min(L_H, dmax):
+ *     below 1e-9 for dmax < 2^16.  An RA call whose bound would exceed 1e-6
+ *     (intermediaries of degree above about 2.2M: dmax >= 2^21 without a
+ *     hub limit below that) is refused with LP_EINVAL and a message naming
+ *     the largest hub limit that keeps it.
  */
 #ifndef LP_H
 #define LP_H
@@ -176,6 +180,26 @@ lp_status lp_predict_range(const lp_graph* g, lp_measure measure, int32_t degree
                            int64_t out_cap, int64_t* out_n);
 
 /*
+ * Merge of global-mode results (the merging phase of Algorithm 1, Section
+ * 4.1.7, across devices): the k best of n_links distinct links (u < v) of
+ * graph g under the total order, sorted.  The intended input is the
+ * concatenation of lp_predict_range results of one measure and degree_cap
+ * over a partition of [0, n): the result is then, bit for bit, what one
+ * lp_predict call returns.  Count measures take each link's exact key from
+ * its cn and the two degrees; AA and RA rebuild their fixed-point sums from
+ * the graph (the score field of the input is not read), so near-equal FP32
+ * scores are ordered exactly as the library's selection orders them.
+ *   links  host lp_link[n_links], any order; k = 0 keeps them all
+ *   out    host lp_link[out_cap]; *out_n receives the number of links kept
+ * LP_EINVAL if a link is not a pair 0 <= u < v < n with cn >= 0, or for the
+ * RA accuracy limit above; LP_ETRUNC as in lp_predict.  Not in the paper's
+ * single-machine design (its merge is sequential over per-thread lists).
+ */
+lp_status lp_merge_links(const lp_graph* g, lp_measure measure, int32_t degree_cap,
+                         const lp_link* links, int64_t n_links, int64_t k, lp_link* out,
+                         int64_t out_cap, int64_t* out_n);
+
+/*
  * Per-source mode: for each sources[i], its k best partners c != sources[i]
  * that are not adjacent to it and score strictly above `threshold`, sorted by
  * (score desc, c asc).  out holds n_src * k links (row i for sources[i]);
@@ -267,13 +291,18 @@ int64_t lp_get_option(lp_option option);
  *   Limits: n_src <= 2^20 and n_src * (40 + 24 k) bytes plus the work items
  *   of the sources must fit in the 32 MiB; larger requests are rejected with
  *   LP_EINVAL and a message (split them into several calls).
- *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.  Calls are serialised on the host, but every
- *   call shares the one array: work that overlaps on the GPU from other
+ *   The array and the code of the kernels this call launches become
+ *   resident on a device when the first graph is created there:
+ *   lp_graph_create looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current) and loads those
+ *   kernels, so no call of this function loads or allocates anything, the
+ *   first one included.  Calls are serialised on the host, but every call
+ *   shares the one array: work that overlaps on the GPU from other
  *   threads or processes using the same library copy must not run at the
  *   same time (it would race on the array).  Per-call state is cleared at
- *   the start of each call.
+ *   the start of each call.  A request whose overflowed or partial work
+ *   items exceed what the array holds also fails with LP_EINVAL and a
+ *   message (use fewer sources per call).
  */
 lp_status lp_predict_sources_static(const lp_graph* g, lp_measure measure, int32_t degree_cap,
                                     const int32_t* d_sources, int32_t n_src, int32_t k,

@@ -2,8 +2,8 @@
 
 Argument marshalling only: every step of the computation runs in the CUDA
 library ``liblp.so`` built from ``csrc/`` (see ``_build.py``).  The names
-mirror the C ABI in ``include/lp.h``.  There is no CPU fallback: importing
-this package fails loudly when the library has not been built.
+mirror the C ABI in ``include/lp.h``.  There is no CPU fallback: every call
+into the library fails loudly (ImportError) when it has not been built.
 """
 from __future__ import annotations
 
@@ -109,6 +109,10 @@ def _load():
     lib.lp_predict_range.argtypes = [_vp, ctypes.c_int, ctypes.c_int32, ctypes.c_int64,
                                      ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _vp,
                                      ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    lib.lp_merge_links.restype = st
+    lib.lp_merge_links.argtypes = [_vp, ctypes.c_int, ctypes.c_int32, _vp, ctypes.c_int64,
+                                   ctypes.c_int64, _vp, ctypes.c_int64,
+                                   ctypes.POINTER(ctypes.c_int64)]
     lib.lp_predict_sources.restype = st
     lib.lp_predict_sources.argtypes = [_vp, ctypes.c_int, ctypes.c_int32, _vp, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.c_double, _vp, _vp]
@@ -250,6 +254,19 @@ def lp_predict_range(h, measure, degree_cap, k: int, src_begin: int, src_end: in
     return out[: cnt.value].copy()
 
 
+def lp_merge_links(h, measure, degree_cap, links, k: int) -> np.ndarray:
+    """The best k of the given global-mode links (an array of LINK_DTYPE, any
+    order) under the library's exact order (host buffers)."""
+    src = np.ascontiguousarray(links, dtype=LINK_DTYPE)
+    cnt = ctypes.c_int64(0)
+    cap_out = min(k, src.size) if k > 0 else src.size
+    out = np.zeros(max(cap_out, 1), dtype=LINK_DTYPE)
+    _check(_load().lp_merge_links(h, _measure(measure), _cap(degree_cap),
+                                  src.ctypes.data if src.size else None, src.size, k,
+                                  out.ctypes.data, cap_out, ctypes.byref(cnt)))
+    return out[: cnt.value].copy()
+
+
 def lp_predict_dev(h, measure, degree_cap, k: int, threshold: float, d_out, out_cap: int) -> int:
     """Global mode into a device buffer (torch tensor or address); returns the
     number of links found."""
@@ -329,6 +346,9 @@ class Graph:
     def predict_range(self, measure, degree_cap, k, src_begin, src_end, threshold=0.0):
         return lp_predict_range(self.handle, measure, degree_cap, k, src_begin, src_end,
                                 threshold)
+
+    def merge(self, measure, degree_cap, links, k):
+        return lp_merge_links(self.handle, measure, degree_cap, links, k)
 
     def predict_sources(self, measure, sources, k, degree_cap=None, threshold=0.0):
         return lp_predict_sources(self.handle, measure, sources, k, degree_cap, threshold)

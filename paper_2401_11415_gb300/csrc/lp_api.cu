@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <atomic>
 #include <climits>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -333,6 +334,9 @@ lp_status lp_graph_create(int32_t n, const int32_t* offsets, const int32_t* indi
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = launch_build_weights(dmax, g->fixbits, g->d_wt, g->stream);
+  // the allocation-free per-source query: its static scratch array and its
+  // kernels become resident here, so that no query loads them
+  if (e == cudaSuccess) e = prepare_static(g->device);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
@@ -510,6 +514,25 @@ ScanArgs base_args_opts(Graph& g, int measure, int cap, double threshold, int mo
   return A;
 }
 
+// RA weights 1/|Gamma_b| are rounded to 2^-F, a relative error of at most
+// |Gamma_b| 2^-(F+1) per weight and so per sum (Eq. 9).  With the largest
+// degree an intermediary can have, min(L_H, dmax), that bound must stay
+// within the 1e-6 contract; beyond it (intermediaries of degree above about
+// 2.2M) the call is refused instead of returning less accurate scores.  AA
+// weights 1/ln|Gamma_b| (Eq. 8) are large enough that the bound is
+// ln|Gamma_b| 2^-(F+1), far below 1e-6 at any degree.
+lp_status accuracy_guard(const Graph& g, int measure, int cap, const char* who) {
+  if (measure != LP_RA) return LP_OK;
+  const long long dbmax = cap < 0 ? (long long)g.dmax : std::min<long long>(cap, g.dmax);
+  const double bound = (double)dbmax * ldexp(1.0, -(g.fixbits + 1));
+  if (bound > 1e-6)
+    return fail(LP_EINVAL,
+                "%s: RA with intermediaries of degree up to %lld would exceed the 1e-6 accuracy "
+                "bound (%.3g); use a hub limit below %lld",
+                who, dbmax, bound, (long long)(1e-6 * ldexp(1.0, g.fixbits + 1)));
+  return LP_OK;
+}
+
 // Split an overflowed hash item into two halves (dense when narrow enough).
 static void split_item(const int4& r, int dense_span, std::vector<int4>& out) {
   int lo = r.y;
@@ -651,6 +674,10 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
   if (src_begin < 0 || src_end < src_begin || src_end > g.n)
     return fail(LP_EINVAL, "lp_predict: source range [%d, %d) outside [0, %d)", src_begin, src_end,
                 g.n);
+  {
+    const lp_status s = accuracy_guard(g, measure, cap, "lp_predict");
+    if (s != LP_OK) return s;
+  }
   if (src_end == src_begin || cap == 0) return LP_OK;
   std::lock_guard<std::mutex> lock(g.mu);
   CU(cudaSetDevice(g.device));
@@ -832,11 +859,86 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
   return LP_OK;
 }
 
+// ------------------------------------------------------------- merging --
+
+// The best k of a set of global-mode links under the total order, with the
+// exact keys of the selection (Section 4.1.7: the merge of lists that
+// independent groups of sources produced).  Count measures take the key from
+// each link's common-neighbour count and the degrees; AA and RA rebuild their
+// fixed-point sums from the graph, so the result equals, bit for bit, what
+// one lp_predict call over all the sources returns.
+static lp_status merge_links(Graph& g, int measure, int cap, const lp_link* links, int64_t n_links,
+                             int64_t k, lp_link* out, int64_t out_cap, int64_t* out_n) {
+  begin_stats();
+  *out_n = 0;
+  if (measure < 0 || measure > LP_RA) return fail(LP_EINVAL, "lp_merge_links: bad measure");
+  if (k < 0 || n_links < 0) return fail(LP_EINVAL, "lp_merge_links: negative k or link count");
+  if (n_links > 0 && !links) return fail(LP_EINVAL, "lp_merge_links: null links");
+  if (out_cap < 0 || (out_cap > 0 && !out))
+    return fail(LP_EINVAL, "lp_merge_links: bad output buffer");
+  for (int64_t i = 0; i < n_links; ++i)
+    if (links[i].u < 0 || links[i].u >= links[i].v || links[i].v >= g.n || links[i].cn < 0)
+      return fail(LP_EINVAL, "lp_merge_links: link %lld is not a pair u < v of the graph",
+                  (long long)i);
+  {
+    const lp_status s = accuracy_guard(g, measure, cap, "lp_merge_links");
+    if (s != LP_OK) return s;
+  }
+  if (n_links == 0) return LP_OK;
+  std::lock_guard<std::mutex> lock(g.mu);
+  CU(cudaSetDevice(g.device));
+  cudaStream_t st = g.stream;
+  const ScanArgs A = base_args(g, measure, cap, 0.0, 0, 0);
+  const u64 n = (u64)n_links;
+  CU(ensure(g, g.s_links, sizeof(lp_link) * n));
+  CU(ensure(g, g.s_buf, sizeof(Cand) * n));
+  CU(ensure(g, g.s_buf2, sizeof(Cand) * n));
+  CU(ensure(g, g.s_buf3, sizeof(Cand) * n));
+  CU(ensure(g, g.s_misc, kMiscBytes));
+  CU(ensure(g, g.s_grp, sizeof(int) * sort_splits_needed(n)));
+  CU(cudaMemcpyAsync(g.s_links.p, links, sizeof(lp_link) * n, cudaMemcpyHostToDevice, st));
+  CU(launch_link_keys(sp<lp_link>(g.s_links), n, measure, g.d_off, g.d_idx, g.d_deg, g.d_arc,
+                      A.cap, A.wt, sp<Cand>(g.s_buf), st));
+  t_stats.launches++;
+  u64 nsorted = n;
+  Cand* res = sp<Cand>(g.s_buf);
+  if (k > 0 && n > (u64)k) {
+    CU(select_best(g, measure, n, (u64)k, &nsorted, /*sorted=*/true));
+    res = sp<Cand>(g.s_buf);
+  } else {
+    CU(launch_sort_cands(res, sp<Cand>(g.s_buf2), sp<int>(g.s_grp), n, st, &res,
+                         &t_stats.launches));
+  }
+  const u64 found = k > 0 ? std::min<u64>(n, (u64)k) : n;
+  *out_n = (int64_t)found;
+  const u64 nwrite = std::min<u64>(found, (u64)out_cap);
+  if (nwrite) {
+    lp_link* d_links = sp<lp_link>(g.s_links);  // the input copy is no longer needed
+    CU(launch_emit_global(res, nwrite, measure, g.fixbits, d_links, st));
+    t_stats.launches++;
+    if (measure == LP_AA || measure == LP_RA) {
+      CU(ensure(g, g.s_pair, pair_groups_scratch(g.n, nwrite)));
+      CU(launch_pair_cn_groups(d_links, nwrite, g.n, g.d_off, g.d_idx, g.d_arc, A.cap, g.s_pair.p,
+                               st, &t_stats.launches));
+    }
+    CU(cudaMemcpyAsync(out, d_links, sizeof(lp_link) * nwrite, cudaMemcpyDeviceToHost, st));
+  }
+  CU(cudaStreamSynchronize(st));
+  if (found > (u64)out_cap)
+    return fail(LP_ETRUNC, "lp_merge_links: %lld links found, room for %lld", (long long)found,
+                (long long)out_cap);
+  return LP_OK;
+}
+
 // ------------------------------------------------------- per-source mode --
 
 static lp_status predict_sources(Graph& g, int measure, int cap, const int* d_src, int n_src, int k,
                                  double threshold, lp_link* d_out, int* d_counts) {
   if (n_src == 0) return LP_OK;
+  {
+    const lp_status s = accuracy_guard(g, measure, cap, "lp_predict_sources");
+    if (s != LP_OK) return s;
+  }
   cudaStream_t st = g.stream;
   Timer tm(g);
   tm.mark(0);
@@ -1055,6 +1157,14 @@ lp_status lp_predict_range(const lp_graph* g, lp_measure measure, int32_t degree
   if (!g || !out_n) return lp::fail(LP_EINVAL, "lp_predict_range: null argument");
   return lp::predict_global(*const_cast<lp_graph*>(g), (int)measure, degree_cap, k, threshold, out,
                             false, out_cap, out_n, src_begin, src_end);
+}
+
+lp_status lp_merge_links(const lp_graph* g, lp_measure measure, int32_t degree_cap,
+                         const lp_link* links, int64_t n_links, int64_t k, lp_link* out,
+                         int64_t out_cap, int64_t* out_n) {
+  if (!g || !out_n) return lp::fail(LP_EINVAL, "lp_merge_links: null argument");
+  return lp::merge_links(*const_cast<lp_graph*>(g), (int)measure, degree_cap, links, n_links, k,
+                         out, out_cap, out_n);
 }
 
 lp_status lp_predict_dev(const lp_graph* g, lp_measure measure, int32_t degree_cap, int64_t k,

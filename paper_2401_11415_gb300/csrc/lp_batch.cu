@@ -78,6 +78,10 @@ bool same_options(const Options& a, const Options& b) {
 // Estimate, bin and record the per-source query of every vertex of g.
 lp_status build_plan(Graph& g, AllPlan& P, int measure, int cap, int k, const Options& opt,
                      lp_link* d_out, int* d_counts) {
+  {
+    const lp_status s = accuracy_guard(g, measure, cap, "batched query");
+    if (s != LP_OK) return s;
+  }
   P.drop_graph();
   cudaStream_t st = g.stream;
   const int n = g.n;

@@ -241,6 +241,12 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
 cudaError_t launch_pair_cn(lp_link* links, const int* cnt_rows, int k, u64 n, const int* off,
                            const int* idx, const int* deg, const Arc* arc, int cap,
                            cudaStream_t st);
+// Exact selection keys of global-mode links: count measures from the link's
+// cn and the degrees, AA / RA by rebuilding the fixed-point sum (wt: the
+// measure's weight table).
+cudaError_t launch_link_keys(const lp_link* links, u64 n, int measure, const int* off,
+                             const int* idx, const int* deg, const Arc* arc, int cap,
+                             const u64* wt, Cand* out, cudaStream_t st);
 constexpr int kRadixBinsHost = 2048;
 cudaError_t radix_select(const Cand* src, u64 n, u64 k, int measure, Cand* sel, Cand* actA,
                          Cand* actB, u32* d_hist, u64* d_cnt, cudaStream_t st, u64* out_n,
@@ -272,10 +278,20 @@ inline T* sp(Graph::Scratch& s) {
 lp_status sources_args_ok(const lp_graph* g, int measure, const void* sources, int n_src, int k,
                           const void* out, const void* counts);
 Graph& graph_of(const lp_graph* g);
+// LP_EINVAL (with a message naming `who`) when RA scores of the hub limit cap
+// could exceed the 1e-6 relative accuracy of the fixed-point sums.
+lp_status accuracy_guard(const Graph& g, int measure, int cap, const char* who);
 // A graph view sharing g's device arrays with its own stream, events and
 // scratch (for concurrent workers); freed with destroy_shadow.
 lp_status make_shadow(const Graph& g, Graph** out);
 void destroy_shadow(Graph* s);
+// Load every kernel of the per-source mode (no launch).
+cudaError_t preload_sources_kernels();
+// Make the allocation-free per-source query ready on the current device dev:
+// look up the device address of its static scratch array (which loads the
+// array's module) and load the kernels it launches.  Called by
+// lp_graph_create, so that no query has to.
+cudaError_t prepare_static(int dev);
 lp_status run_sources_dev(Graph& g, int measure, int cap, const int* d_src, int n_src, int k,
                           double threshold, lp_link* d_out, int* d_counts);
 }  // namespace lp

@@ -12,10 +12,14 @@
 // host heap.
 //
 // The array is a host-side symbol: its device address is looked up with
-// cudaGetSymbolAddress once per device (on the first call on that device,
-// with that device current) and the address is what the kernels receive.
-// Every call uses the same array, so calls that overlap on the GPU race on
-// it; the per-call counters are cleared at the start of each call.
+// cudaGetSymbolAddress once per device, with that device current, and the
+// address is what the kernels receive.  The lookup is what makes the array
+// (and the code of its module) resident on the device, so it is done when a
+// graph is created on that device (prepare_static, called by
+// lp_graph_create), together with loading every kernel the per-source path
+// launches: a query never performs it.  Every call uses the same array, so
+// calls that overlap on the GPU race on it; the per-call counters are
+// cleared at the start of each call.
 #include <mutex>
 
 #include "lp_internal.cuh"
@@ -43,24 +47,33 @@ constexpr int kStaticMaxSources = 1 << 20;
 static int h_cnt[kStaticMaxSources];   // zero between calls
 static int h_pos[kStaticMaxSources];
 
-// Device address of the array on the current device.
-static cudaError_t static_scratch(int dev, void** out) {
-  if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_static_ptr[dev] = p;
-  }
-  *out = g_static_ptr[dev];
-  return cudaSuccess;
-}
-
 __global__ void k_static_check_sources(const int* __restrict__ s, int n_src, int n,
                                        u32* __restrict__ bad) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n_src && (s[i] < 0 || s[i] >= n)) atomicExch(bad, 1u);
+}
+
+// Device address of the array on device dev (current), looked up once.
+cudaError_t prepare_static(int dev) {
+  if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (g_static_ptr[dev]) return cudaSuccess;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, k_static_check_sources);
+  if (e == cudaSuccess) e = preload_sources_kernels();
+  if (e != cudaSuccess) return e;
+  g_static_ptr[dev] = p;
+  return cudaSuccess;
+}
+
+// The address prepared for device dev, or null if no graph was created there.
+static void* static_scratch(int dev) {
+  if (dev < 0 || dev >= kStaticMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  return g_static_ptr[dev];
 }
 
 // Bump allocator over the static array.
@@ -81,9 +94,15 @@ struct Arena {
 static lp_status run_static(Graph& g, int measure, int cap, const int* d_src, int n_src, int k,
                             double threshold, lp_link* d_out, int* d_counts) {
   cudaStream_t st = g.stream;
-  void* base = nullptr;
-  cudaError_t e = static_scratch(g.device, &base);
-  if (e != cudaSuccess) return report_cuda(e, "lp_predict_sources_static: cudaGetSymbolAddress");
+  {
+    const lp_status s = accuracy_guard(g, measure, cap, "lp_predict_sources_static");
+    if (s != LP_OK) return s;
+  }
+  void* base = static_scratch(g.device);
+  if (!base)
+    return report_error(LP_EINTERNAL,
+                        "lp_predict_sources_static: static scratch not prepared on this device");
+  cudaError_t e = cudaSuccess;
   Arena ar{reinterpret_cast<unsigned char*>(base), 0, kStaticScratchBytes};
   Counters* d_ctr = ar.take<Counters>(1);
   int4* warpq = ar.take<int4>((size_t)n_src + 1);
@@ -162,14 +181,28 @@ static lp_status run_static(Graph& g, int measure, int cap, const int* d_src, in
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return report_cuda(e, "lp_predict_sources_static: scan");
+    if (h.error == 2u)  // more overflowed items than the split records hold
+      return report_error(LP_EINVAL,
+                          "lp_predict_sources_static: the sources overflow more work items than "
+                          "the static scratch can re-split in one round; use fewer sources per call");
+    if (h.error == 3u)  // more partial lists than the static scratch holds
+      return report_error(LP_EINVAL,
+                          "lp_predict_sources_static: the sources need more partial lists than the "
+                          "static scratch holds; use fewer sources per call");
     if (h.error) return report_error(LP_EINTERNAL, "lp_predict_sources_static: device check failed");
     stats_add((int64_t)h.candidates, (int32_t)h.nsplit, 0);
     npartial = h.npartial;
+    if (npartial > (u64)kStaticMaxPartials)
+      return report_error(LP_EINVAL,
+                          "lp_predict_sources_static: the sources need more partial lists than "
+                          "can be merged in one call (65536); use fewer sources per call");
     nw = nm = nc = 0;
     if (h.nsplit == 0) break;
     // overflowed hash items: run again as two halves (dense when narrow)
     if (h.nsplit > (u64)kStaticMaxSplits)
-      return report_error(LP_EINTERNAL, "lp_predict_sources_static: too many split items");
+      return report_error(LP_EINVAL,
+                          "lp_predict_sources_static: too many overflowed items to re-split; use "
+                          "fewer sources per call");
     e = cudaMemcpy(h_splits, split, sizeof(int4) * h.nsplit, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return report_cuda(e, "lp_predict_sources_static: splits");
     u64 nh = 0;
@@ -193,8 +226,6 @@ static lp_status run_static(Graph& g, int measure, int cap, const int* d_src, in
     nc = nh;
   }
   if (npartial) {
-    if (npartial > (u64)kStaticMaxPartials)
-      return report_error(LP_EINVAL, "lp_predict_sources_static: too many partial lists");
     e = cudaMemcpy(h_hdr, phdr, sizeof(int2) * npartial, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return report_cuda(e, "lp_predict_sources_static: partials");
     // group the partial lists by record: counting sort over the records

@@ -2019,21 +2019,22 @@ __global__ void k_emit_sources(const TopEnt* __restrict__ top, const int* __rest
   out[i] = make_link(measure, sources[r], x.c, x.num, x.den, (u64)x.cn, fixbits);
 }
 
-// Common neighbours b of (u, v) with |Gamma_b| <= cap, one warp per link
-// (AA / RA lists, whose tables hold weight sums rather than counts).  x is
-// the endpoint of smaller degree.  Short Gamma_x (or a much longer Gamma_y):
-// each lane takes elements b of Gamma_x (hub test from the arc table) and
-// looks the other endpoint up in the shorter of Gamma_b and Gamma_y.  Two
-// long lists of similar length: a merge-path intersection across the lanes.
-__global__ void k_pair_cn(lp_link* __restrict__ links, const int* __restrict__ cnt_rows, int k,
-                          u64 n, const int* __restrict__ off, const int* __restrict__ idx,
-                          const int* __restrict__ deg, const Arc* __restrict__ arc, int cap) {
-  const u64 gw = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// Sum over the common neighbours b of (u, v) with |Gamma_b| <= cap of 1
+// (wt null: the count) or of wt[|Gamma_b|] (the AA / RA fixed-point weight,
+// so the sum is the key the scan accumulated: integer addition does not
+// depend on the order).  One warp per pair; every lane returns the total.
+// x is the endpoint of smaller degree.  Short Gamma_x (or a much longer
+// Gamma_y): each lane takes elements b of Gamma_x (hub test from the arc
+// table) and looks the other endpoint up in the shorter of Gamma_b and
+// Gamma_y.  Two long lists of similar length: a merge-path intersection
+// across the lanes.
+__device__ __forceinline__ u64 pair_common(int u, int v, const int* __restrict__ off,
+                                           const int* __restrict__ idx,
+                                           const int* __restrict__ deg,
+                                           const Arc* __restrict__ arc, int cap,
+                                           const u64* __restrict__ wt) {
   const int lane = lane_id();
-  if (gw >= n) return;
-  if (cnt_rows && (int)(gw % k) >= cnt_rows[gw / k]) return;
-  const lp_link L = links[gw];
-  int x = L.u, y = L.v;
+  int x = u, y = v;
   if (off[x + 1] - off[x] > off[y + 1] - off[y]) {
     const int t = x;
     x = y;
@@ -2043,7 +2044,7 @@ __global__ void k_pair_cn(lp_link* __restrict__ links, const int* __restrict__ c
   const int ys = off[y], ye = off[y + 1];
   const int dy = ye - ys;
   const int dx = xe - xs;
-  int c = 0;
+  u64 c = 0;
   if (dx <= 64 || dy > 16 * dx || cap < 256) {
     // short Gamma_x, a much longer Gamma_y or a low hub limit (most b are
     // skipped without a search): look each b of Gamma_x up
@@ -2051,14 +2052,16 @@ __global__ void k_pair_cn(lp_link* __restrict__ links, const int* __restrict__ c
       const Arc t = arc[e];  // b = t.w, |Gamma_b| = t.z, Gamma_b ends at t.y
       const int b = t.w, db = t.z;
       if (db > cap) continue;
+      bool hit;
       if (db <= dy) {
         const int be = t.y, bs = be - db;
         const int p = lower_bound_interp(idx, bs, be, y);
-        c += (p < be && __ldg(idx + p) == y) ? 1 : 0;
+        hit = p < be && __ldg(idx + p) == y;
       } else {
         const int p = lower_bound_interp(idx, ys, ye, b);
-        c += (p < ye && __ldg(idx + p) == b) ? 1 : 0;
+        hit = p < ye && __ldg(idx + p) == b;
       }
+      if (hit) c += wt ? __ldg(wt + db) : 1ull;
     }
   } else {
     // comparable long lists: both walked in 32-element tiles, one element
@@ -2080,8 +2083,12 @@ __global__ void k_pair_cn(lp_link* __restrict__ links, const int* __restrict__ c
         if (__shfl_sync(FULLMASK, yv, p + step - 1) < xv) p += step;
       const int yp = __shfl_sync(FULLMASK, yv, p);  // every lane takes part
       bool hit = xv != INT_MAX && yp == xv;
-      if (hit && cap < INT_MAX) hit = __ldg(deg + xv) <= cap;
-      c += hit ? 1 : 0;
+      int db = 0;
+      if (hit && (cap < INT_MAX || wt)) {
+        db = __ldg(deg + xv);
+        hit = db <= cap;
+      }
+      if (hit) c += wt ? __ldg(wt + db) : 1ull;
       const int lx = __shfl_sync(FULLMASK, xv, 31), ly = __shfl_sync(FULLMASK, yv, 31);
       if (lx <= ly) {
         i += 32;
@@ -2095,8 +2102,45 @@ __global__ void k_pair_cn(lp_link* __restrict__ links, const int* __restrict__ c
       }
     }
   }
-  c = __reduce_add_sync(FULLMASK, (u32)c);
-  if (lane == 0) links[gw].cn = c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULLMASK, c, o);
+  return c;
+}
+
+// Common neighbours of AA / RA links (whose tables hold weight sums rather
+// than counts), one warp per link.
+__global__ void k_pair_cn(lp_link* __restrict__ links, const int* __restrict__ cnt_rows, int k,
+                          u64 n, const int* __restrict__ off, const int* __restrict__ idx,
+                          const int* __restrict__ deg, const Arc* __restrict__ arc, int cap) {
+  const u64 gw = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= n) return;
+  if (cnt_rows && (int)(gw % k) >= cnt_rows[gw / k]) return;
+  const lp_link L = links[gw];
+  const u64 c = pair_common(L.u, L.v, off, idx, deg, arc, cap, nullptr);
+  if (lane_id() == 0) links[gw].cn = (int)c;
+}
+
+// Exact selection keys of global-mode links (u < v): the count measures'
+// rational from the link's common-neighbour count and the two degrees (Eq.
+// 1-7), AA / RA's fixed-point sum rebuilt from the graph (Eq. 8-9).  One warp
+// per link.
+__global__ void k_link_keys(const lp_link* __restrict__ links, u64 n, int measure,
+                            const int* __restrict__ off, const int* __restrict__ idx,
+                            const int* __restrict__ deg, const Arc* __restrict__ arc, int cap,
+                            const u64* __restrict__ wt, Cand* __restrict__ out) {
+  const u64 gw = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= n) return;
+  const lp_link L = links[gw];
+  Cand x;
+  x.u = L.u;
+  x.v = L.v;
+  if (measure == LP_AA || measure == LP_RA) {
+    x.num = pair_common(L.u, L.v, off, idx, deg, arc, cap, wt);
+    x.den = 1;
+  } else {
+    make_key(measure, (u64)L.cn, (u64)__ldg(deg + L.u), (u64)__ldg(deg + L.v), x.num, x.den);
+  }
+  if (lane_id() == 0) out[gw] = x;
 }
 
 // ------------------------------------------------------------ launchers ---
@@ -2232,6 +2276,34 @@ cudaError_t launch_scan_med(const ScanArgs& A, const int4* q, u64 nq, cudaStream
              : launch_cta_t<false, 1, kMedThreads>(A, q, nq, tb, claim, st);
 }
 
+// Load the code of every kernel the per-source mode launches, without
+// launching any (cudaFuncGetAttributes loads a kernel that lazy module loading
+// has not loaded yet; loading can allocate device memory for the code).
+cudaError_t preload_sources_kernels() {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaSuccess;
+  auto get = [&](auto kern) {
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+  };
+  auto big = [&](auto kern) {
+    if (e == cudaSuccess) e = allow_max_smem(kern);
+  };
+  get(k_estimate<1, false>);
+  get(k_estimate<1, true>);
+  big(k_scan_warp<false, 1>);
+  big(k_scan_warp<true, 1>);
+  big(k_scan_cta<false, 1, kMedThreads>);
+  big(k_scan_cta<true, 1, kMedThreads>);
+  big(k_scan_big<false, 1, 512>);
+  big(k_scan_big<true, 1, 512>);
+  big(k_scan_big<false, 1, 1024>);
+  big(k_scan_big<true, 1, 1024>);
+  get(k_merge_partials);
+  get(k_emit_sources);
+  get(k_pair_cn);
+  return e;
+}
+
 cudaError_t launch_merge_partials(const int4* grp_list, int ngrp, const int* order,
                                   const TopEnt* partial, const int2* hdr, int k, TopEnt* out_top,
                                   int* out_cnt, cudaStream_t st) {
@@ -2257,6 +2329,16 @@ cudaError_t launch_emit_sources(const TopEnt* top, const int* cnt, const int* so
   if (n == 0) return cudaSuccess;
   k_emit_sources<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(top, cnt, sources, n_src, k, measure,
                                                                fixbits, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_link_keys(const lp_link* links, u64 n, int measure, const int* off,
+                             const int* idx, const int* deg, const Arc* arc, int cap,
+                             const u64* wt, Cand* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const u64 threads = 256;
+  k_link_keys<<<(unsigned)((n * 32 + threads - 1) / threads), (unsigned)threads, 0, st>>>(
+      links, n, measure, off, idx, deg, arc, cap, wt, out);
   return cudaGetLastError();
 }
 

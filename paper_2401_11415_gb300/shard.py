@@ -9,20 +9,17 @@ result.  The global mode needs exactly one exchange: the ranks' lists are
 all-gathered and merged (``predict_distributed``).  The per-source mode needs
 none (its rows just concatenate).
 
+This module only partitions, gathers and hands the lists to a merge.  The
+merge is the library's ``lp_merge_links`` (``library_merge``): it orders the
+links by the exact keys of the library's own selection (rebuilt on the
+device), so the merged list equals one ``lp_predict`` call bit for bit.
+
 ``shard_bounds`` balances the ranges by an upper bound of each source's wedge
 work (the degrees of its intermediaries that pass the hub test).
-``merge_topk`` orders the count measures exactly, by the rational key
-recomputed from the common-neighbour count and the two degrees; AA and RA by
-their FP32 score (the lists agree with the unsharded call up to pairs within
-FP32 rounding of each other).
 """
 from __future__ import annotations
 
-from fractions import Fraction
-
 import numpy as np
-
-COUNT_MEASURES = ("CN", "JC", "SI", "SC", "HP", "HD", "LHN")
 
 
 def shard_bounds(off, idx, nshards: int, degree_cap=None) -> list[int]:
@@ -49,59 +46,38 @@ def shard_bounds(off, idx, nshards: int, degree_cap=None) -> list[int]:
     return bounds
 
 
-def _key(measure: str, cn: int, du: int, dv: int):
-    """The exact ordering key of a count measure (Eq. 1-7, Salton through its
-    square), as the library defines it."""
-    if measure == "CN":
-        return Fraction(cn)
-    if measure == "JC":
-        return Fraction(cn, du + dv - cn)
-    if measure == "SI":
-        return Fraction(cn, du + dv)
-    if measure == "SC":
-        return Fraction(cn * cn, du * dv)
-    if measure == "HP":
-        return Fraction(cn, min(du, dv))
-    if measure == "HD":
-        return Fraction(cn, max(du, dv))
-    if measure == "LHN":
-        return Fraction(cn, du * dv)
-    raise ValueError(measure)
-
-
-def merge_topk(parts, k: int, measure: str, deg) -> np.ndarray:
-    """The best k links of the union of the sorted lists in `parts` (arrays of
-    the library's link dtype) under (score desc, u asc, v asc); `deg` is the
-    degree array of the graph."""
+def gather_parts(parts):
+    """One array of the links of every non-empty part (the merge input)."""
     given = [p for p in parts if p is not None]
     nonempty = [p for p in given if len(p)]
-    if not nonempty:
-        return np.zeros(0, dtype=given[0].dtype) if given else np.zeros(0)
-    allp = np.concatenate(nonempty)
-    u = allp["u"].astype(np.int64)
-    v = allp["v"].astype(np.int64)
-    if measure in COUNT_MEASURES:
-        deg = np.asarray(deg, dtype=np.int64)
-        keys = [_key(measure, int(c), int(deg[a]), int(deg[b]))
-                for c, a, b in zip(allp["cn"].tolist(), u.tolist(), v.tolist())]
-        order = sorted(range(len(allp)), key=lambda i: (-keys[i], u[i], v[i]))
-        order = np.asarray(order, dtype=np.int64)
-    else:
-        order = np.lexsort((v, u, -allp["score"].astype(np.float64)))
-    return allp[order[: max(k, 0)]].copy()
+    if nonempty:
+        return np.concatenate(nonempty)
+    if given:
+        return np.zeros(0, dtype=given[0].dtype)
+    from . import LINK_DTYPE
+    return np.zeros(0, dtype=LINK_DTYPE)
 
 
-def predict_sharded(predict_range, n: int, bounds, measure: str, degree_cap, k: int, deg,
+def library_merge(graph, measure: str, degree_cap):
+    """merge(parts, k) through lp_merge_links on `graph` (a Graph whose
+    lp_predict_range produced the parts)."""
+    def merge(parts, k):
+        return graph.merge(measure, degree_cap, gather_parts(parts), k)
+    return merge
+
+
+def predict_sharded(predict_range, merge, bounds, measure: str, degree_cap, k: int,
                     threshold: float = 0.0) -> np.ndarray:
     """Run every range in turn (one process, e.g. one GPU standing in for
     several) and merge.  predict_range(measure, cap, k, begin, end, threshold)
-    returns a range's sorted best k (Graph.predict_range)."""
+    returns a range's sorted best k (Graph.predict_range); merge(parts, k)
+    returns the best k of their union (library_merge)."""
     parts = [predict_range(measure, degree_cap, k, bounds[i], bounds[i + 1], threshold)
              for i in range(len(bounds) - 1)]
-    return merge_topk(parts, k, measure, deg)
+    return merge(parts, k)
 
 
-def predict_distributed(predict_range, bounds, measure: str, degree_cap, k: int, deg,
+def predict_distributed(predict_range, merge, bounds, measure: str, degree_cap, k: int,
                         threshold: float = 0.0, group=None) -> np.ndarray:
     """One range per rank of the default torch.distributed group (len(bounds)
     = world size + 1): the rank's best k, one all_gather of the lists, and the
@@ -114,4 +90,4 @@ def predict_distributed(predict_range, bounds, measure: str, degree_cap, k: int,
     mine = predict_range(measure, degree_cap, k, bounds[rank], bounds[rank + 1], threshold)
     parts = [None] * world
     dist.all_gather_object(parts, mine, group=group)
-    return merge_topk(parts, k, measure, deg)
+    return merge(parts, k)

@@ -14,6 +14,9 @@ that the oracle computes one by one, and by properties that hold at any size.
 * Chung-Lu 4,194,304 vertices, global top-200,000 DLH(256) AA and RA:
   sampled links' common-neighbour counts and scores against the oracle
   (vertex ids in several bitmap windows).
+* R-MAT scale 24 with 10% held out, global top-|E^U| (about 26M links) for
+  JC and RA at hub limit 256: sampled links and sampled sources against the
+  oracle, as at scale 20.
 * R-MAT scale 24 (the serving graph): top-10 DLH(256) RA requests of 1, 300
   and 4096 sources, sampled rows against the oracle.
 """
@@ -70,13 +73,40 @@ def test_rmat20_global_sampled(lp, rmat20, measure, cap):
     k = len(rmat20.hu)
     with lp.Graph.from_csr(g) as G:
         got = G.predict(measure, cap, k)
+    _check_global_sampled(g, got, k, measure, cap, 0)
+
+
+@pytest.fixture(scope="module")
+def rmat24():
+    return L.cfg_rmat24()
+
+
+@pytest.mark.parametrize("measure", ["JC", "RA"])
+def test_rmat24_global_sampled(lp, rmat24, measure):
+    """The largest global configuration: R-MAT scale 24 with 10% held out,
+    DLH(256), N_P = |E^U| (about 26M links), in the launch configuration of
+    the benchmark's scale-24 record; sampled links and sampled sources
+    against the oracle as at scale 20."""
+    split = L.holdout(rmat24, 0.1, seed=43)
+    g = split.observed
+    k = len(split.hu)
+    with lp.Graph.from_csr(g) as G:
+        got = G.predict(measure, 256, k)
+    _check_global_sampled(g, got, k, measure, 256, 24)
+
+
+def _check_global_sampled(g, got, k, measure, cap, salt):
+    """Order and pair invariants of the whole list, sampled links re-scored
+    by the oracle's pair scorer, and completeness of sampled sources: every
+    pair of the source that ranks before the last link is in the list, and
+    nothing else of it is."""
     assert 0 < len(got) <= k
     u = got["u"].astype(np.int64)
     v = got["v"].astype(np.int64)
     assert (u < v).all() and (u >= 0).all() and (v < g.n).all()
     assert len(np.unique(u * g.n + v)) == len(got)
     assert (np.diff(got["score"]) <= 0).all()
-    rng = np.random.default_rng({"JC": 1000, "RA": 2000}[measure] + (cap or 0))
+    rng = np.random.default_rng({"JC": 1000, "RA": 2000}[measure] + (cap or 0) + 7919 * salt)
     # sampled links against the pair scorer
     for i in rng.choice(len(got), 150, replace=False).tolist() + [0, len(got) - 1]:
         r, adj = oracle.pair(g.n, g.off, g.idx, measure, int(u[i]), int(v[i]), cap)
@@ -203,8 +233,8 @@ def test_grid_per_source_all_vertices(lp):
             assert (counts > 0).all()
 
 
-def test_rmat24_serving_requests(lp):
-    g = L.cfg_rmat24()
+def test_rmat24_serving_requests(lp, rmat24):
+    g = rmat24
     rng = np.random.default_rng(11)
     deg = np.diff(g.off)
     live = np.nonzero(deg > 0)[0]

@@ -226,3 +226,42 @@ def test_truncation_status(lp, cfg1):
         st = lp.lib().lp_predict(G.handle, 1, -1, 100, 0.0, out.ctypes.data, 40, ctypes.byref(n))
         assert st == lp.LP_ETRUNC and n.value == 100
         assert out.tobytes() == full[:40].tobytes()
+
+
+def _star_with_path(leaves):
+    """Star K_{1,leaves} (centre 0) plus a 3-edge path beside it."""
+    n = leaves + 4
+    u = np.concatenate([np.zeros(leaves, np.int32), np.array([leaves + 1, leaves + 2], np.int32)])
+    v = np.concatenate([np.arange(1, leaves + 1, dtype=np.int32),
+                        np.array([leaves + 2, leaves + 3], np.int32)])
+    return L.from_edges(n, u, v)
+
+
+def test_ra_accuracy_guard(lp):
+    """RA weights 1/|Gamma_b| (Eq. 9) are rounded to 2^-F fraction bits, a
+    relative error of up to |Gamma_b| 2^-(F+1).  A star whose centre has
+    2^21 + 1 leaves keeps that within 1e-6 and must match the oracle; with
+    2^21 + 2^18 leaves it would not, so IBase RA is refused with LP_EINVAL
+    while a hub limit that drops the centre, and AA (weights 1/ln|Gamma_b|),
+    are still answered and match the oracle."""
+    from parity import compare_sources
+    for leaves, refused in ((2 ** 21 + 1, False), (2 ** 21 + 2 ** 18, True)):
+        g = _star_with_path(leaves)
+        src = np.array([1, leaves, leaves + 1], np.int32)
+        with lp.Graph.from_csr(g) as G:
+            runs = [("AA", None), ("RA", 1 << 20)]
+            if refused:
+                with pytest.raises(lp.LPError) as e:
+                    G.predict_sources("RA", src, 4, None)
+                assert e.value.status == lp.LP_EINVAL
+                with pytest.raises(lp.LPError) as e:
+                    G.predict("RA", None, 10)
+                assert e.value.status == lp.LP_EINVAL
+            else:
+                runs.append(("RA", None))
+            for m, cap in runs:
+                gl, gc = G.predict_sources(m, src, 4, cap)
+                ol, oc = oracle.predict_sources(g.n, g.off, g.idx, m, src, 4, cap)
+                compare_sources(gl, gc, ol, oc, m, g, src, cap)
+                if cap is None:
+                    assert gc[0] == 4 and gc[1] == 4  # leaves meet every other leaf

@@ -1,7 +1,8 @@
 """lp_serve_*: continuous batching of per-source queries (needs a GPU).
 
 Each served result must equal lp_predict_sources on the same sources alone,
-whatever else is in the batch; requests of uneven sizes and different
+whatever else is in the batch, and a quarter of the served requests (all four
+kinds of query) are checked row by row against the CPU oracle; requests of uneven sizes and different
 (measure, hub limit, k) arrive from several threads.  Bounded waits, a full
 queue and bad requests are made on the host side (a paused server), never by
 stalling the GPU.
@@ -12,6 +13,8 @@ import numpy as np
 import pytest
 
 import lp_inputs as L
+import oracle
+from parity import compare_sources
 
 pytestmark = pytest.mark.gpu
 
@@ -65,6 +68,14 @@ def test_served_equals_alone(lp, graph):
         for (gl, gc), (el, ec) in zip(got, expect):
             assert np.array_equal(gc, ec)
             assert gl.tobytes() == el.tobytes()
+        # the served rows themselves against the oracle: a quarter of the
+        # requests (j % 16 in {0, 5, 10, 15} covers all four kinds of query)
+        for j in range(len(reqs)):
+            if j % 16 not in (0, 5, 10, 15):
+                continue
+            src, (m, cap, k) = reqs[j]
+            ol, oc = oracle.predict_sources(g.n, g.off, g.idx, m, src, k, cap)
+            compare_sources(got[j][0], got[j][1], ol, oc, m, g, src, cap)
 
 
 def test_paused_timeout_full_queue_and_errors(lp, graph):
