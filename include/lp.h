@@ -109,18 +109,24 @@ typedef struct {
   float ms_scan;
   float ms_select;
   float ms_total;
-  /* per scan kernel: [0] warp tier, [1] medium tier, [2] large tier */
-  int64_t tier_wedges[3];  /* wedges of the sources binned to the tier       */
-  int64_t tier_arcs[3];    /* arc-table entries read by the tier             */
-  int64_t tier_kept[3];    /* of which pass the hub test                     */
-  int32_t tier_launches[3];/* launches of the tier's scan kernel             */
-  float tier_ms[3];        /* summed device time of those launches (timing on) */
+  /* per scan kernel: [0] warp tier, [1] medium tier, [2] large tier,
+     [3] expand-and-count tier (global mode; its time includes the arc and
+     expand passes, its launches count the count-pass launches) */
+  int64_t tier_wedges[4];  /* wedges of the sources binned to the tier       */
+  int64_t tier_arcs[4];    /* arc-table entries read by the tier             */
+  int64_t tier_kept[4];    /* of which pass the hub test                     */
+  int32_t tier_launches[4];/* launches of the tier's scan kernel             */
+  float tier_ms[4];        /* summed device time of those launches (timing on) */
   int64_t phase_cycles[6]; /* LP_OPT_PHASE_PROFILE: SM cycles of the large tier
                               (summed over CTAs) in [0] item setup, [1] arc
                               segments and short walks, [3] long-segment
                               pieces, [4] exclusion and scoring, [5] item end;
                               [2] is the whole time of dense items (also in
                               the others)                                     */
+  float ms_expand;         /* device time of the expand-and-count tier's arc and
+                              expand passes (timing on; also in tier_ms[3])   */
+  int32_t exp_units;       /* sources of the expand-and-count tier            */
+  int32_t exp_batches;     /* their expand batches                            */
 } lp_stats;
 
 /*
@@ -233,9 +239,18 @@ typedef enum {
                                  (1024..2^30, 262144)                           */
   LP_OPT_PHASE_PROFILE = 8,   /* 1: record per-phase clock cycles of the large
                                  tier in lp_stats.phase_cycles (0..1, 0)        */
-  LP_OPT_BIG_CTA_THREADS = 9  /* threads of a large-tier CTA: 1024 (one per SM,
+  LP_OPT_BIG_CTA_THREADS = 9, /* threads of a large-tier CTA: 1024 (one per SM,
                                  192 KB table) or 512 (two per SM, 98 KB each;
                                  split targets shrink with the table) (1024)   */
+  LP_OPT_EXPAND = 10,         /* global mode: large sources that would be cut
+                                 into several id-range items are instead
+                                 expanded once into per-bucket records and
+                                 counted bucket by bucket: 0 never, 1 always,
+                                 2 when the index array exceeds 128 MB (2)     */
+  LP_OPT_EXPAND_BATCH = 11,   /* wedges expanded per batch of that tier
+                                 (2^16..2^34, 2^29; 4 bytes each, 8 for AA/RA) */
+  LP_OPT_EXPAND_HASH_LOGCAP = 12 /* log2 slots of that tier's hash tables (6..14,
+                                 14); a bucket whose table fills is re-split */
 } lp_option;
 
 /*

@@ -43,10 +43,11 @@ class lp_stats(ctypes.Structure):
                 ("splits", ctypes.c_int32), ("compactions", ctypes.c_int32),
                 ("launches", ctypes.c_int32), ("ms_estimate", ctypes.c_float),
                 ("ms_scan", ctypes.c_float), ("ms_select", ctypes.c_float),
-                ("ms_total", ctypes.c_float), ("tier_wedges", ctypes.c_int64 * 3),
-                ("tier_arcs", ctypes.c_int64 * 3), ("tier_kept", ctypes.c_int64 * 3),
-                ("tier_launches", ctypes.c_int32 * 3), ("tier_ms", ctypes.c_float * 3),
-                ("phase_cycles", ctypes.c_int64 * 6)]
+                ("ms_total", ctypes.c_float), ("tier_wedges", ctypes.c_int64 * 4),
+                ("tier_arcs", ctypes.c_int64 * 4), ("tier_kept", ctypes.c_int64 * 4),
+                ("tier_launches", ctypes.c_int32 * 4), ("tier_ms", ctypes.c_float * 4),
+                ("phase_cycles", ctypes.c_int64 * 6), ("ms_expand", ctypes.c_float),
+                ("exp_units", ctypes.c_int32), ("exp_batches", ctypes.c_int32)]
 
 
 class lp_serve_opts(ctypes.Structure):
@@ -305,7 +306,8 @@ def lp_predict_sources_static(h, measure, d_sources, n_src: int, k: int, degree_
 
 LP_OPT_SELECT_BUFFER, LP_OPT_WARP_MAX_WEDGES, LP_OPT_CTA_MAX_WEDGES, LP_OPT_SPLIT_TARGET, \
     LP_OPT_SPLIT_LOGCAP, LP_OPT_MED_MAX_WEDGES, LP_OPT_ITEM_WEDGES, LP_OPT_PHASE_PROFILE, \
-    LP_OPT_BIG_CTA_THREADS = range(1, 10)
+    LP_OPT_BIG_CTA_THREADS, LP_OPT_EXPAND, LP_OPT_EXPAND_BATCH, \
+    LP_OPT_EXPAND_HASH_LOGCAP = range(1, 13)
 
 
 def lp_set_option(option: int, value: int) -> None:

@@ -129,7 +129,10 @@ static void free_graph(Graph* g) {
                            &g->s_thresh, &g->s_vfloor, &g->s_pair, &g->s_gcur, &g->s_flags,
                            &g->s_partial,
                            &g->s_phdr, &g->s_top,
-                           &g->s_cnt, &g->s_links, &g->s_src, &g->s_grp};
+                           &g->s_cnt, &g->s_links, &g->s_src, &g->s_grp, &g->s_xq, &g->s_xw,
+                           &g->s_xunit, &g->s_xaseg, &g->s_xaoff, &g->s_xadeg, &g->s_xrec,
+                           &g->s_xtile, &g->s_xtunit, &g->s_xpre, &g->s_xbunit, &g->s_countq,
+                           &g->s_countq2};
   for (auto* s : all)
     if (s->p) cudaFree(s->p);
   if (g->owns_arrays) {
@@ -142,6 +145,8 @@ static void free_graph(Graph* g) {
   for (auto& e : g->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : g->kev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : g->xev)
     if (e) cudaEventDestroy(e);
   if (g->stream) cudaStreamDestroy(g->stream);
   delete static_cast<lp_graph*>(g);
@@ -184,6 +189,18 @@ lp_status lp_set_option(lp_option option, int64_t value) {
       if (value != 512 && value != 1024) break;
       lp::g_opt.big_threads = (int)value;
       return LP_OK;
+    case LP_OPT_EXPAND:
+      if (value < 0 || value > 2) break;
+      lp::g_opt.expand = (int)value;
+      return LP_OK;
+    case LP_OPT_EXPAND_BATCH:
+      if (value < (1 << 16) || value > (1ll << 34)) break;
+      lp::g_opt.expand_batch = value;
+      return LP_OK;
+    case LP_OPT_EXPAND_HASH_LOGCAP:
+      if (value < 6 || value > 14) break;
+      lp::g_opt.expand_logcap = (int)value;
+      return LP_OK;
     case LP_OPT_CTA_MAX_WEDGES:
       if (value < 257 || value > lp::kCtaMaxWedges) break;
       lp::g_opt.cta_max = (int)value;
@@ -215,6 +232,9 @@ int64_t lp_get_option(lp_option option) {
     case LP_OPT_ITEM_WEDGES: return o.item_wedges;
     case LP_OPT_PHASE_PROFILE: return o.phase_profile;
     case LP_OPT_BIG_CTA_THREADS: return o.big_threads;
+    case LP_OPT_EXPAND: return o.expand;
+    case LP_OPT_EXPAND_BATCH: return o.expand_batch;
+    case LP_OPT_EXPAND_HASH_LOGCAP: return o.expand_logcap;
     default: return -1;
   }
 }
@@ -319,7 +339,8 @@ lp_status lp_graph_create(int32_t n, const int32_t* offsets, const int32_t* indi
   if (e == cudaSuccess) e = cudaMalloc(&g->d_wt, sizeof(u64) * 2 * ((size_t)dmax + 1));
   if (e == cudaSuccess) e = cudaMalloc(&d_err, sizeof(int));
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->ev[i]);
-  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->kev[i]);
+  for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->kev[i]);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&g->xev[i]);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(g->d_off, offsets, sizeof(int) * ((size_t)n + 1), cudaMemcpyHostToDevice,
                         g->stream);
@@ -384,9 +405,9 @@ struct Timer {
 // The three work queues (warp tier, medium tier, large tier).  cur[t] holds
 // the records of the next launch, alt[t] receives the rebuilt queue.
 struct Queues {
-  Graph::Scratch* cur[3];
-  Graph::Scratch* alt[3];
-  u64 n[3];
+  Graph::Scratch* cur[4];
+  Graph::Scratch* alt[4];
+  u64 n[4];
 };
 
 // Launch the scan kernels; with timing on, time each on the graph's stream.
@@ -395,13 +416,15 @@ struct Queues {
 static cudaError_t scan_launches(Graph& g, const ScanArgs& A, const Queues& Q, bool timing,
                                  u64 large_limit = ~0ull) {
   cudaStream_t st = g.stream;
-  for (int t = 0; t < 3; ++t) {
+  for (int t = 0; t < 4; ++t) {
     const u64 n = t == 2 ? std::min(Q.n[t], large_limit) : Q.n[t];
     if (!n) continue;
     if (timing) cudaEventRecord(g.kev[2 * t], st);
     const int4* q = sp<int4>(*Q.cur[t]);
-    cudaError_t e = t == 0 ? launch_scan_warp(A, q, n, st)
-                           : (t == 1 ? launch_scan_med(A, q, n, st) : launch_scan_cta(A, q, n, st));
+    cudaError_t e = t == 0   ? launch_scan_warp(A, q, n, st)
+                    : t == 1 ? launch_scan_med(A, q, n, st)
+                    : t == 2 ? launch_scan_cta(A, q, n, st)
+                             : launch_exp_count(A, q, n, st);
     if (e != cudaSuccess) return e;
     if (timing) cudaEventRecord(g.kev[2 * t + 1], st);
     t_stats.tier_launches[t]++;
@@ -413,7 +436,7 @@ static cudaError_t scan_launches(Graph& g, const ScanArgs& A, const Queues& Q, b
 // After the stream synchronised: add the kernels' event times to the stats.
 static void scan_times(Graph& g, const Queues& Q, bool timing) {
   if (!timing) return;
-  for (int t = 0; t < 3; ++t) {
+  for (int t = 0; t < 4; ++t) {
     float ms = 0.f;
     if (Q.n[t] && cudaEventElapsedTime(&ms, g.kev[2 * t], g.kev[2 * t + 1]) == cudaSuccess)
       t_stats.tier_ms[t] += ms;
@@ -427,7 +450,7 @@ static void estimate_stats(const Counters& h) {
   t_stats.warp_sources = (int32_t)h.nwarp;
   t_stats.cta_items = (int32_t)(h.nmed + h.nitem);
   t_stats.dense_items = (int32_t)h.dense_items;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 4; ++i) {
     t_stats.tier_wedges[i] = (int64_t)h.tier_wedges[i];
     t_stats.tier_arcs[i] = (int64_t)h.tier_arcs[i];
     t_stats.tier_kept[i] = (int64_t)h.tier_kept[i];
@@ -580,7 +603,7 @@ static cudaError_t build_queue(Graph& g, Graph::Scratch& dst, const std::vector<
 // remainder of each queue.
 static cudaError_t rebuild_queues(Graph& g, Queues& Q, const std::vector<int4>* heads,
                                   const u64* done) {
-  for (int t = 0; t < 3; ++t) {
+  for (int t = 0; t < 4; ++t) {
     u64 n2 = 0;
     cudaError_t e = build_queue(g, *Q.alt[t], heads[t], sp<int4>(*Q.cur[t]), done[t], Q.n[t], &n2);
     if (e != cudaSuccess) return e;
@@ -593,7 +616,16 @@ static cudaError_t rebuild_queues(Graph& g, Queues& Q, const std::vector<int4>* 
 static int record_tier(const int4& r) {
   if (r.w & (1 << 30)) return 0;
   if (r.w & (1 << 29)) return 1;
+  if (r.w & kExpItem) return 3;
   return 2;
+}
+
+// An overflowed count item of the expand-and-count tier: its id range in
+// halves (a range narrower than the table's fill limit cannot overflow).
+static void split_count_item(const int4& r, std::vector<int4>& out) {
+  const int mid = r.y + (r.z - r.y) / 2;
+  out.push_back(make_int4(r.x, r.y, mid, r.w | kExpSplit));
+  out.push_back(make_int4(r.x, mid, r.z, r.w | kExpSplit));
 }
 
 __global__ void k_set_flags(const int4* __restrict__ rec, int n, unsigned char* __restrict__ flag,
@@ -615,6 +647,15 @@ static lp_status run_estimate(Graph& g, ScanArgs& A, int n_rec, int2* grp, Count
   CU(ensure(g, g.s_medq, sizeof(int4) * ((size_t)n_rec + 1)));
   u64 itemq_cap = std::max<u64>(1024, g.s_itemq.bytes / sizeof(int4));
   CU(ensure(g, g.s_itemq, sizeof(int4) * itemq_cap));
+  u64 xq_cap = 0;
+  if (A.expand) {
+    xq_cap = std::max<u64>(1024, g.s_xq.bytes / sizeof(int4));
+    CU(ensure(g, g.s_xq, sizeof(int4) * xq_cap));
+    CU(ensure(g, g.s_xw, sizeof(u64) * xq_cap));
+    A.xq = sp<int4>(g.s_xq);
+    A.xw = sp<u64>(g.s_xw);
+    A.xq_cap = xq_cap;
+  }
   for (int attempt = 0; attempt < 3; ++attempt) {
     CU(cudaMemsetAsync(d_ctr, 0, sizeof(Counters), st));
     A.ctr = d_ctr;
@@ -623,11 +664,21 @@ static lp_status run_estimate(Graph& g, ScanArgs& A, int n_rec, int2* grp, Count
     t_stats.launches++;
     CU(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    if (h.nitem <= itemq_cap) break;
-    itemq_cap = h.nitem + 1024;
-    CU(ensure(g, g.s_itemq, sizeof(int4) * itemq_cap));
+    if (h.nitem <= itemq_cap && h.nexp <= xq_cap) break;
+    if (h.nitem > itemq_cap) {
+      itemq_cap = h.nitem + 1024;
+      CU(ensure(g, g.s_itemq, sizeof(int4) * itemq_cap));
+    }
+    if (h.nexp > xq_cap) {
+      xq_cap = h.nexp + 1024;
+      CU(ensure(g, g.s_xq, sizeof(int4) * xq_cap));
+      CU(ensure(g, g.s_xw, sizeof(u64) * xq_cap));
+      A.xq = sp<int4>(g.s_xq);
+      A.xw = sp<u64>(g.s_xw);
+      A.xq_cap = xq_cap;
+    }
   }
-  if (h.nitem > itemq_cap) return fail(LP_EINTERNAL, "item queue sizing");
+  if (h.nitem > itemq_cap || h.nexp > xq_cap) return fail(LP_EINTERNAL, "item queue sizing");
   estimate_stats(h);
   return LP_OK;
 }
@@ -687,6 +738,11 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
   ScanArgs A = base_args(g, measure, cap, threshold, 0, 0);
   A.rec_base = src_begin;
   CU(attach_cursors(g, A));
+  const Options opt = options_snapshot();
+  // the expand-and-count tier pays off where the index array does not stay
+  // in the L2 cache (window sweeps then pay DRAM round trips per arc)
+  A.expand = opt.expand == 1 || (opt.expand == 2 && g.arcs * (int64_t)sizeof(int) > (128ll << 20));
+  A.x_logcap = opt.expand_logcap;
   // selection buffer
   const u64 minbuf = (u64)std::max<long long>(16, options_snapshot().select_buffer);
   u64 C = k > 0 ? std::max<u64>(minbuf, 2ull * (u64)k + std::min<u64>(minbuf, 1ull << 20)) : minbuf;
@@ -709,15 +765,38 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
   Counters h{};
   lp_status s = run_estimate(g, A, src_end - src_begin, nullptr, h);
   if (s != LP_OK) return s;
+  ExpState X;
+  if (h.nexp) {
+    s = exp_setup(g, A, h.nexp, opt.expand_batch, tm.on, X);
+    if (s != LP_OK) return s;
+    t_stats.launches += X.launches;
+    X.launches = 0;
+  }
   tm.mark(1);
 
-  Queues Q = {{&g.s_warpq, &g.s_medq, &g.s_itemq}, {&g.s_warpq2, &g.s_medq2, &g.s_itemq2},
-              {h.nwarp, h.nmed, h.nitem}};
+  Queues Q = {{&g.s_warpq, &g.s_medq, &g.s_itemq, &g.s_countq},
+              {&g.s_warpq2, &g.s_medq2, &g.s_itemq2, &g.s_countq2},
+              {h.nwarp, h.nmed, h.nitem, 0}};
   u64 kept = 0;  // valid entries at the start of the buffer
-  std::vector<int4> failed, splits;
-  std::vector<int4> heads[3];
-  for (int round = 0; Q.n[0] + Q.n[1] + Q.n[2] > 0; ++round) {
+  std::vector<int4> failed, splits, xitems;
+  std::vector<int4> heads[4];
+  for (int round = 0; Q.n[0] + Q.n[1] + Q.n[2] + Q.n[3] > 0 || X.next < X.batches.size();
+       ++round) {
     if (round > 100000) return fail(LP_EINTERNAL, "lp_predict: no progress");
+    // first round: the small tiers and an eighth of the large tier (items
+    // in source order, a sample of the sources), so that the threshold they
+    // set (a compaction below) already filters the rest of the large tier
+    // and every batch of the expand-and-count tier
+    const bool seed = round == 0 && k > 0 && (Q.n[2] >= 64 || !X.batches.empty());
+    const u64 large_n = seed && Q.n[2] >= 64 ? Q.n[2] / 8 : Q.n[2];
+    if (!seed && Q.n[3] == 0 && X.next < X.batches.size()) {
+      // the previous batch's items are all done: expand the next one
+      s = exp_next_batch(g, A, X, tm.on, xitems);
+      if (s != LP_OK) return s;
+      t_stats.launches += X.launches;
+      X.launches = 0;
+      CU(build_queue(g, *Q.cur[3], xitems, nullptr, 0, 0, &Q.n[3]));
+    }
     Counters z{};
     z.cand_cnt = kept;
     CU(cudaMemcpyAsync(d_ctr, &z, sizeof(Counters), cudaMemcpyHostToDevice, st));
@@ -730,12 +809,7 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
     A.failed_cap = failed_cap;
     A.split = sp<int4>(g.s_split);
     A.split_cap = split_cap;
-    A.prof = options_snapshot().phase_profile ? d_ctr->prof : nullptr;
-    // first round: the small tiers and an eighth of the large tier (items
-    // in source order, a sample of the sources), so that the threshold they
-    // set (a compaction below) already filters the rest of the large tier
-    const bool seed = round == 0 && k > 0 && Q.n[2] >= 64;
-    const u64 large_n = seed ? Q.n[2] / 8 : Q.n[2];
+    A.prof = opt.phase_profile ? d_ctr->prof : nullptr;
     CU(scan_launches(g, A, Q, tm.on, large_n));
     CU(cudaMemcpyAsync(&h, d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
@@ -749,8 +823,8 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
       CU(cudaMemcpy(failed.data(), g.s_failed.p, sizeof(int4) * h.nfailed, cudaMemcpyDeviceToHost));
     if (h.nsplit)
       CU(cudaMemcpy(splits.data(), g.s_split.p, sizeof(int4) * h.nsplit, cudaMemcpyDeviceToHost));
-    const u64 done[3] = {std::min<u64>(h.claim_w, Q.n[0]), std::min<u64>(h.claim_m, Q.n[1]),
-                         std::min<u64>(h.claim_c, large_n)};
+    const u64 done[4] = {std::min<u64>(h.claim_w, Q.n[0]), std::min<u64>(h.claim_m, Q.n[1]),
+                         std::min<u64>(h.claim_c, large_n), std::min<u64>(h.claim_x, Q.n[3])};
     const u64 valid = std::min<u64>(h.cand_cnt, C);
     t_stats.splits += (int32_t)h.nsplit;
     if (h.full || (seed && valid >= (u64)k)) {
@@ -794,7 +868,7 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
         kept = m;
       }
       // guarantee room for progress
-      const bool progress = (done[0] + done[1] + done[2]) > h.nfailed;
+      const bool progress = (done[0] + done[1] + done[2] + done[3]) > h.nfailed;
       if (k == 0 || !progress || C - kept < (C >> 2)) {
         const u64 C2 = C * 2;
         CU(ensure(g, g.s_buf2, sizeof(Cand) * C2));
@@ -811,9 +885,16 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
     }
     for (auto& hd : heads) hd.clear();
     for (const int4& r : failed) heads[record_tier(r)].push_back(r);
-    for (const int4& r : splits) split_item(r, A.big_span, heads[2]);
+    for (const int4& r : splits) {
+      if (r.w & kExpItem) split_count_item(r, heads[3]);
+      else split_item(r, A.big_span, heads[2]);
+    }
     CU(rebuild_queues(g, Q, heads, done));
   }
+  t_stats.tier_ms[3] += X.ms_expand;
+  t_stats.ms_expand = X.ms_expand;
+  t_stats.exp_units = (int32_t)X.units.size();
+  t_stats.exp_batches = (int32_t)X.batches.size();
   tm.mark(2);
   // final selection: the best k, sorted
   u64 nsorted = kept;
@@ -1121,7 +1202,8 @@ lp_status make_shadow(const Graph& g, Graph** out) {
   cudaError_t e = cudaSetDevice(g.device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->ev[i]);
-  for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->kev[i]);
+  for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->kev[i]);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->xev[i]);
   if (e != cudaSuccess) {
     free_graph(s);
     return cuda_fail(e, "shadow graph");

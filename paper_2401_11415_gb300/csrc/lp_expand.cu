@@ -1,0 +1,657 @@
+// lp_expand.cu -- the expand-and-count large tier of the global mode.
+//
+// Algorithm 1 counts, for a source a, the paths a -> b -> c (c > a) through
+// intermediaries b with |Gamma_b| <= L_H into a table indexed by c
+// (scanEdges; Sections 4.1.2-4.1.3, 4.2.1).  For a source whose second-order
+// vertices spread over more ids than one shared-memory table covers, the
+// window sweeps of the large tier revisit every arc of the source once per
+// id window; when the index array does not stay in the L2 cache those visits
+// are DRAM round trips and cost far more than the wedges themselves.  This
+// tier reads every wedge once instead:
+//
+//  * arc pass (k_exp_arcs, one CTA per source): the kept arcs' c > a
+//    suffixes, compacted, with their running wedge offsets;
+//  * expand pass (k_exp_tiles, one CTA per tile of consecutive arcs): every
+//    wedge's c (with |Gamma_b| for AA / RA) is read once, streamed by the
+//    warp-cooperative wedge loop, histogrammed by bucket (an id range of
+//    2^wlog) in shared memory, and written back grouped by bucket within the
+//    tile, with the tile's bucket starts;
+//  * count pass (k_exp_count, one CTA per bucket): the bucket's records from
+//    every tile of the source are counted in shared memory -- dense counters
+//    when the source's wedges are dense in its id range, else a hash table
+//    -- then the first-order neighbours are dropped (Section 4.1.4) and the
+//    counters scored and admitted exactly as in the other tiers (Eq. 1-9,
+//    count floor, admission threshold; Sections 4.1.5-4.1.6).
+//
+// Records are the only extra traffic: 4 bytes per wedge written and read
+// back (8 for AA / RA), against the per-arc round trips of every window.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "lp_internal.cuh"
+#include "lp_scan_dev.cuh"
+
+namespace lp {
+
+constexpr int kExpThreads = 256;  // arc and expand passes
+constexpr int kCountThreads = 1024;
+
+// Exclusive CTA-wide prefix sums of two ints per thread (ex, ey) and their
+// totals.  wsum: 2 * (threads / 32) ints of shared memory; one barrier, and
+// wsum must not be written again before the caller's next barrier.
+template <int THREADS>
+__device__ __forceinline__ void exp_scan2(int x, int y, int& ex, int& ey, int& tx, int& ty,
+                                          int* wsum) {
+  constexpr int NW = THREADS / 32;
+  const int lane = lane_id(), wid = threadIdx.x >> 5;
+  int ix = x, iy = y;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int ux = __shfl_up_sync(FULLMASK, ix, o);
+    const int uy = __shfl_up_sync(FULLMASK, iy, o);
+    if (lane >= o) {
+      ix += ux;
+      iy += uy;
+    }
+  }
+  if (lane == 31) {
+    wsum[wid] = ix;
+    wsum[NW + wid] = iy;
+  }
+  __syncthreads();
+  int bx = 0, by = 0;
+  tx = ty = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const int vx = wsum[w], vy = wsum[NW + w];
+    if (w < wid) {
+      bx += vx;
+      by += vy;
+    }
+    tx += vx;
+    ty += vy;
+  }
+  ex = bx + ix - x;
+  ey = by + iy - y;
+}
+
+// ------------------------------------------------------------- arc pass --
+
+// One CTA per unit: the kept arcs (|Gamma_b| <= L_H) with a nonempty c > a
+// suffix of Gamma_b, compacted: aseg = first index of the suffix in idx, aoff
+// = wedges of the unit before it (aoff[K] = W), adeg = |Gamma_b| (AA / RA).
+__global__ void __launch_bounds__(kExpThreads) k_exp_arcs(ScanArgs A, ExpUnit* __restrict__ units,
+                                                           int nunits, int* __restrict__ aseg,
+                                                           int* __restrict__ aoff,
+                                                           int* __restrict__ adeg) {
+  __shared__ int wsum[2 * (kExpThreads / 32)];
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int a = units[u].a;
+    const long long base = units[u].arc_base;
+    const int e0 = A.off[a], e1 = A.off[a + 1];
+    int carry = 0, cnt = 0;
+    for (int eb = e0; eb < e1; eb += kExpThreads) {  // CTA-uniform trips
+      const int e = eb + threadIdx.x;
+      int s0 = 0, len = 0, db = 0;
+      if (e < e1) {
+        const Arc t = A.arc[e];
+        if (t.z <= A.cap) {
+          s0 = t.x + 1;
+          len = t.y - s0;
+          db = t.z;
+        }
+      }
+      if (len < 0) len = 0;
+      const int nz = len > 0 ? 1 : 0;
+      int elen, enz, tlen, tnz;
+      exp_scan2<kExpThreads>(len, nz, elen, enz, tlen, tnz, wsum);
+      if (nz) {
+        const long long k = base + cnt + enz;
+        aseg[k] = s0;
+        aoff[k] = carry + elen;
+        if (adeg) adeg[k] = db;
+      }
+      carry += tlen;
+      cnt += tnz;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      aoff[base + cnt] = carry;
+      units[u].K = cnt;
+      if ((long long)carry != units[u].W) atomicExch(&A.ctr->error, 4u);
+    }
+  }
+}
+
+// ----------------------------------------------------------- expand pass --
+
+// One CTA per tile: the arcs of the unit whose first wedge lies in
+// [tl * tile_w, (tl + 1) * tile_w).  Two passes over their wedges (the
+// second from the cache): a bucket histogram, then every record written to
+// its bucket's slot within the tile.
+template <bool V64>
+__global__ void __launch_bounds__(kExpThreads) k_exp_tiles(ScanArgs A, const ExpUnit* __restrict__ units,
+                                                           const int* __restrict__ tile_unit,
+                                                           int ntiles, const int* __restrict__ aseg,
+                                                           const int* __restrict__ aoff,
+                                                           const int* __restrict__ adeg,
+                                                           void* __restrict__ rec,
+                                                           u64* __restrict__ tile_rec,
+                                                           int* __restrict__ pre) {
+  constexpr int NW = kExpThreads / 32;
+  __shared__ int hist[kExpMaxBuckets];
+  __shared__ int wsum[2 * NW];
+  __shared__ int s_j0, s_j1;
+  const int lane = lane_id(), wid = threadIdx.x >> 5;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int u = tile_unit[t];
+    const ExpUnit U = units[u];
+    const long long tl = t - U.tile_base;
+    const int* off_u = aoff + U.arc_base;
+    if (threadIdx.x == 0) {
+      // first arc starting at or after each tile boundary
+      const long long w0 = tl * U.tile_w, w1 = w0 + U.tile_w;
+      int l = 0, r = U.K;
+      while (l < r) {
+        const int m = (l + r) >> 1;
+        if (off_u[m] < w0) l = m + 1; else r = m;
+      }
+      s_j0 = l;
+      r = U.K;
+      while (l < r) {
+        const int m = (l + r) >> 1;
+        if (off_u[m] < w1) l = m + 1; else r = m;
+      }
+      s_j1 = l;
+    }
+    for (int b = threadIdx.x; b < U.nb; b += kExpThreads) hist[b] = 0;
+    __syncthreads();
+    const int j0 = s_j0, j1 = s_j1;
+    const int lo = U.lo, wlog = U.wlog;
+    // pass 1: bucket histogram
+    for (int jb = j0 + wid * 32; jb < j1; jb += NW * 32) {  // warp-uniform trips
+      const int j = jb + lane;
+      int s = 0, len = 0;
+      if (j < j1) {
+        s = aseg[U.arc_base + j];
+        len = off_u[j + 1] - off_u[j];
+      }
+      scan_arcs<int>(s, len, 0, A.idx, [&](int c, int) { atomicAdd(&hist[(c - lo) >> wlog], 1); });
+    }
+    __syncthreads();
+    // exclusive prefix of the histogram (each thread a run of buckets); the
+    // starts become the write cursors and the tile's bucket-start table
+    const int per = (U.nb + kExpThreads - 1) / kExpThreads;
+    const int b0 = min(U.nb, threadIdx.x * per), b1 = min(U.nb, b0 + per);
+    int run = 0;
+    for (int b = b0; b < b1; ++b) run += hist[b];
+    int ex, ey, tot, tot2;
+    exp_scan2<kExpThreads>(run, 0, ex, ey, tot, tot2, wsum);
+    int* pt = pre + U.pre_base + tl * (U.nb + 1);
+    for (int b = b0; b < b1; ++b) {
+      const int h = hist[b];
+      hist[b] = ex;
+      pt[b] = ex;
+      ex += h;
+    }
+    if (threadIdx.x == 0) {
+      pt[U.nb] = tot;
+      tile_rec[t] = (u64)(U.rec_base + (j0 < U.K ? off_u[j0] : off_u[U.K]));
+    }
+    const u64 rb = (u64)(U.rec_base + (j0 < U.K ? off_u[j0] : off_u[U.K]));
+    __syncthreads();
+    // pass 2: every record to its bucket's next slot
+    for (int jb = j0 + wid * 32; jb < j1; jb += NW * 32) {  // warp-uniform trips
+      const int j = jb + lane;
+      int s = 0, len = 0, db = 0;
+      if (j < j1) {
+        s = aseg[U.arc_base + j];
+        len = off_u[j + 1] - off_u[j];
+        if (V64) db = adeg[U.arc_base + j];
+      }
+      scan_arcs<int>(s, len, db, A.idx, [&](int c, int w) {
+        const int pos = atomicAdd(&hist[(c - lo) >> wlog], 1);
+        if (V64) reinterpret_cast<int2*>(rec)[rb + pos] = make_int2(c, w);
+        else reinterpret_cast<int*>(rec)[rb + pos] = c;
+      });
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ count pass --
+
+// One CTA per count item {a, clo, chi, batch bucket | kExpItem}: the records
+// of the bucket (from every tile of the unit) with clo <= c < chi are counted
+// in shared memory, the first-order neighbours dropped, and the counters
+// scored and admitted.  A hash item whose table fills is handed back for
+// splitting; a dense item cannot overflow.
+template <bool V64, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) k_exp_count(ScanArgs A, const int4* __restrict__ q,
+                                                          u64 nq, int table_bytes,
+                                                          u64* __restrict__ claim) {
+  typedef typename std::conditional<V64, u64, u32>::type V;
+  constexpr int NW = THREADS / 32;
+  const int kLogcap = A.x_logcap;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int max_slots = 1 << (ceil_log2((u64)table_bytes / (4 + sizeof(V)) + 1) - 1);
+  int* keys = reinterpret_cast<int*>(smem);
+  V* vals = reinterpret_cast<V*>(smem + (size_t)max_slots * 4);
+  u32* words = reinterpret_cast<u32*>(smem);
+  __shared__ int4 s_rec;
+  __shared__ u64 s_next;
+  __shared__ int s_ndistinct, s_overflow, s_fail, s_e0, s_e1;
+  const int lane = lane_id(), wid = threadIdx.x >> 5;
+  for (int i = threadIdx.x * 16; i < table_bytes; i += THREADS * 16)
+    *reinterpret_cast<int4*>(smem + i) = make_int4(0, 0, 0, 0);
+  const Thresh T = *A.thresh;
+  u64 n_cand = 0;
+  if (threadIdx.x == 0) {
+    if (*(volatile u32*)&A.ctr->full) s_next = ~0ull;
+    else s_next = atomicAdd(claim, 1ull);
+  }
+  __syncthreads();
+  for (;;) {
+    const u64 qi = s_next;
+    if (qi >= nq) break;
+    if (threadIdx.x == 0) {
+      s_rec = q[qi];
+      s_fail = 0;
+      s_ndistinct = 0;
+      s_overflow = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // look-ahead claim, read after the item
+      if (*(volatile u32*)&A.ctr->full) s_next = ~0ull;
+      else s_next = atomicAdd(claim, 1ull);
+    }
+    const int4 rec = s_rec;
+    const int a = rec.x, clo = rec.y, chi = rec.z;
+    const int gb = rec.w & kExpGbMask;
+    const int u = A.xbucket_unit[gb];
+    const ExpUnit U = A.xunit[u];
+    const int b = (int)(gb - U.bucket_base);
+    const bool dense = (U.flags & kExpDense) != 0;
+    const int cw = U.flags & 3;
+    const int lg = clo, hg = chi;
+    const int nslots = 1 << kLogcap;
+    const int limit = (nslots * 3) / 4;
+    u32* dlo = words;
+    u32* dhi = words + (1 << U.wlog);
+    auto insert = [&](int c, V wc) {
+      if (dense) {
+        const int p = swz(c - lg);
+        if (cw == kExpC8) {
+          atomicAdd(words + (p >> 2), 1u << ((p & 3) << 3));
+        } else if (cw == kExpC16) {
+          atomicAdd(words + (p >> 1), 1u << ((p & 1) << 4));
+        } else if (cw == kExpC32) {
+          atomicAdd(words + p, (u32)wc);
+        } else {  // split halves: low word, then high word plus carry
+          const u32 l = (u32)wc, h = (u32)((u64)wc >> 32);
+          const u32 old = atomicAdd(dlo + p, l);
+          const u32 hc = h + ((old + l < old) ? 1u : 0u);
+          if (hc) atomicAdd(dhi + p, hc);
+        }
+      } else {
+        if (*(volatile int*)&s_overflow) return;
+        const int rc = hash_add<V>(keys, vals, kLogcap, c, wc);
+        if (rc == 1) {
+          if (atomicAdd(&s_ndistinct, 1) >= limit) s_overflow = 1;
+        } else if (rc == 2) {
+          s_overflow = 1;
+        }
+      }
+    };
+    // insert the bucket's records, warps taking the tiles round-robin
+    for (int tt = wid; tt < U.T; tt += NW) {  // warp-uniform trips
+      const long long tb = U.tile_base + tt;
+      const int* pt = A.xpre + U.pre_base + (long long)tt * (U.nb + 1) + b;
+      const int p0 = pt[0], p1 = pt[1];
+      const u64 rb = A.xtile_rec[tb];
+      for (int i = p0 + lane; i < p1; i += 32) {
+        int c;
+        V w;
+        if (V64) {
+          const int2 r = reinterpret_cast<const int2*>(A.xrec)[rb + i];
+          c = r.x;
+          w = (V)__ldg(A.wt + r.y);
+        } else {
+          c = reinterpret_cast<const int*>(A.xrec)[rb + i];
+          w = (V)1;
+        }
+        if (c >= clo && c < chi) insert(c, w);
+      }
+      if (!dense && *(volatile int*)&s_overflow) break;
+    }
+    __syncthreads();
+    if (!dense && s_overflow) {
+      // hand the item back for splitting; leave the table empty
+      for (int i = threadIdx.x * 4; i < nslots; i += THREADS * 4) {
+        *reinterpret_cast<int4*>(keys + i) = make_int4(0, 0, 0, 0);
+        zero4<V>(vals + i);
+      }
+      if (threadIdx.x == 0) {
+        const u64 f = atomicAdd(&A.ctr->nsplit, 1ull);
+        if (f < A.split_cap) A.split[f] = rec;
+        else A.ctr->error = 2u;
+      }
+      __syncthreads();
+      continue;
+    }
+    // drop the first-order neighbours c in [max(clo, a + 1), chi)
+    if (threadIdx.x == 0) {
+      const int e0 = A.off[a], e1 = A.off[a + 1];
+      const int l = lower_bound_g(A.idx, e0, e1, max(clo, a + 1));
+      s_e0 = l;
+      s_e1 = lower_bound_g(A.idx, l, e1, chi);
+    }
+    __syncthreads();
+    for (int e = s_e0 + threadIdx.x; e < s_e1; e += THREADS) {
+      const int c = __ldg(A.idx + e);
+      if (dense) {
+        const int p = swz(c - lg);
+        if (cw == kExpC8) atomicAnd(words + (p >> 2), ~(0xffu << ((p & 3) << 3)));
+        else if (cw == kExpC16) atomicAnd(words + (p >> 1), ~(0xffffu << ((p & 1) << 4)));
+        else if (cw == kExpC32) words[p] = 0;
+        else {
+          dlo[p] = 0;
+          dhi[p] = 0;
+        }
+      } else {
+        hash_kill<V>(keys, vals, kLogcap, c);
+      }
+    }
+    __syncthreads();
+    // score: every counter or slot once; the ones below the count floor of
+    // the source's degree are only counted
+    const u64 da = (u64)(A.off[a + 1] - A.off[a]);
+    const u64 vmin = T.valid ? __ldg(A.vfloor + da) : 1;
+    bool fail = false;
+    int qn = 0, qc = 0, qd = 0;
+    V qv = 0;
+    const int npos = (hg - lg + 31) & ~31;
+    if (dense && cw == kExpC8) {
+      u32 q8 = (u32)qv;
+      for (int base0 = wid * 256; base0 < npos; base0 += THREADS * 8)  // warp-uniform trips
+        fail |= score_dense8_linear(A, T, a, da, words, base0, npos, lg, vmin, n_cand, qn, qc, q8,
+                                    qd);
+      qv = (V)q8;
+    } else if (dense && cw == kExpC16) {
+      u32 q16 = (u32)qv;
+      for (int base0 = wid * 256; base0 < npos; base0 += THREADS * 8)  // warp-uniform trips
+        fail |= score_dense16_linear(A, T, a, da, words, base0, npos, lg, vmin, n_cand, qn, qc,
+                                     q16, qd);
+      qv = (V)q16;
+    } else if (dense && cw == kExpC32) {
+      u32 q32 = (u32)qv;
+      for (int base0 = wid * 128; base0 < npos; base0 += THREADS * 4)  // warp-uniform trips
+        fail |= score_dense_linear<u32>(A, T, a, da, words, base0, npos, lg, vmin, n_cand, qn, qc,
+                                        q32, qd);
+      qv = (V)q32;
+    } else if (dense) {
+      u64 q64 = (u64)qv;
+      for (int base0 = wid * 128; base0 < npos; base0 += THREADS * 4)  // warp-uniform trips
+        fail |= score_dense64_linear(A, T, a, da, dlo, dhi, base0, npos, lg, vmin, n_cand, qn, qc,
+                                     q64, qd);
+      qv = (V)q64;
+    } else if (T.valid) {
+      for (int base0 = wid * 128; base0 < nslots; base0 += THREADS * 4)
+        fail |= score_hash_linear<V>(A, T, a, da, keys, vals, base0, nslots, vmin, n_cand, qn, qc,
+                                     qv, qd);
+    } else {
+      int tcnt = 0;
+      for (int base0 = wid * 128; base0 < nslots; base0 += THREADS * 4)
+        fail |= score_hash_chunk<V, 0>(A, T, a, da, keys, vals, base0, nslots, nullptr, tcnt,
+                                       n_cand);
+    }
+    if (qn > 0) fail |= survivors_flush<V>(A, T, a, da, qn, qc, qv, qd);
+    if (fail && lane == 0) s_fail = 1;
+    __syncthreads();
+    if (threadIdx.x == 0 && s_fail) {
+      A.ctr->full = 1u;
+      const u64 f = atomicAdd(&A.ctr->nfailed, 1ull);
+      if (f < A.failed_cap) A.failed[f] = rec;
+      else A.ctr->error = 1u;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) n_cand += __shfl_xor_sync(FULLMASK, n_cand, o);
+  if (lane == 0 && n_cand) atomicAdd(&A.ctr->candidates, n_cand);
+}
+
+// ------------------------------------------------------------- launchers --
+
+cudaError_t launch_exp_arcs(const ScanArgs& A, ExpUnit* units, int nunits, int* aseg, int* aoff,
+                            int* adeg, cudaStream_t st) {
+  if (nunits <= 0) return cudaSuccess;
+  int dev = 0, nsm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = std::min(nunits, nsm * 8);
+  k_exp_arcs<<<blocks, kExpThreads, 0, st>>>(A, units, nunits, aseg, aoff, adeg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exp_tiles(const ScanArgs& A, const ExpUnit* units, const int* tile_unit,
+                             int ntiles, const int* aseg, const int* aoff, const int* adeg,
+                             void* rec, u64* tile_rec, int* pre, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  int dev = 0, nsm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = std::min(ntiles, nsm * 6);
+  if (A.measure == LP_AA || A.measure == LP_RA)
+    k_exp_tiles<true><<<blocks, kExpThreads, 0, st>>>(A, units, tile_unit, ntiles, aseg, aoff,
+                                                       adeg, rec, tile_rec, pre);
+  else
+    k_exp_tiles<false><<<blocks, kExpThreads, 0, st>>>(A, units, tile_unit, ntiles, aseg, aoff,
+                                                        adeg, rec, tile_rec, pre);
+  return cudaGetLastError();
+}
+
+template <bool V64>
+static cudaError_t launch_count_t(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st) {
+  auto kern = k_exp_count<V64, kCountThreads>;
+  const int tb = kCtaSmem;  // dense windows use 128 KB of it, hash tables up to all
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  int dev = 0, optin = 0, nsm = 1;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+  if (e != cudaSuccess) return e;
+  const int blocks = (int)std::max<u64>(1, std::min<u64>((u64)nsm, nq));
+  kern<<<blocks, kCountThreads, (size_t)tb, st>>>(A, q, nq, tb, &A.ctr->claim_x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exp_count(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st) {
+  if (nq == 0) return cudaSuccess;
+  if (A.measure == LP_AA || A.measure == LP_RA) return launch_count_t<true>(A, q, nq, st);
+  return launch_count_t<false>(A, q, nq, st);
+}
+
+}  // namespace lp
+
+// ------------------------------------------------------------ host plan --
+
+namespace lp {
+
+namespace {
+
+constexpr double kDenseMinRecords = 4096;  // expected records per window for dense counting
+// expected records per hash bucket: half the table's slots
+
+int floor_log2(double x) {
+  int l = 0;
+  while (l < 62 && std::ldexp(1.0, l + 1) <= x) ++l;
+  return l;
+}
+
+#define XCU(x)                                             \
+  do {                                                     \
+    cudaError_t e_ = (x);                                  \
+    if (e_ != cudaSuccess) return report_cuda(e_, #x);     \
+  } while (0)
+
+}  // namespace
+
+lp_status exp_setup(Graph& g, ScanArgs& A, u64 nexp, long long batch_wedges, bool timing,
+                    ExpState& S) {
+  S = ExpState();
+  if (nexp == 0) return LP_OK;
+  cudaStream_t st = g.stream;
+  std::vector<int4> q(nexp);
+  std::vector<u64> w(nexp);
+  XCU(cudaMemcpyAsync(q.data(), g.s_xq.p, sizeof(int4) * nexp, cudaMemcpyDeviceToHost, st));
+  XCU(cudaMemcpyAsync(w.data(), g.s_xw.p, sizeof(u64) * nexp, cudaMemcpyDeviceToHost, st));
+  XCU(cudaStreamSynchronize(st));
+  const bool v64 = A.measure == LP_AA || A.measure == LP_RA;
+  S.units.resize(nexp);
+  long long arcs = 0;
+  u64 wmax = 0;
+  for (u64 i = 0; i < nexp; ++i) {
+    ExpUnit U;
+    memset(&U, 0, sizeof(U));
+    U.a = q[i].x;
+    U.lo = q[i].y;
+    U.hi = q[i].z;
+    U.kept = q[i].w;
+    U.W = (long long)w[i];
+    const double span = (double)std::max(1, U.hi - U.lo);
+    // counter width of a dense window: a count never exceeds the kept arcs
+    int cw, wd;
+    if (v64) {
+      cw = kExpC64;
+      wd = 14;
+    } else if (U.kept <= 255) {
+      cw = kExpC8;
+      wd = 17;
+    } else if (U.kept <= 65535) {
+      cw = kExpC16;
+      wd = 16;
+    } else {
+      cw = kExpC32;
+      wd = 15;
+    }
+    const double nb_dense = std::ceil(span / std::ldexp(1.0, wd));
+    const double per_window = (double)U.W * std::ldexp(1.0, wd) / span;
+    if (per_window >= kDenseMinRecords && nb_dense <= kExpMaxBuckets) {
+      U.flags = kExpDense | cw;
+      U.wlog = wd;
+    } else {
+      U.flags = cw;
+      const double per_bucket = std::ldexp(1.0, A.x_logcap - 1);
+      U.wlog = std::max(0, floor_log2(per_bucket * span / (double)std::max<long long>(1, U.W)));
+      while (std::ceil(span / std::ldexp(1.0, U.wlog)) > kExpMaxBuckets) ++U.wlog;
+    }
+    U.nb = (int)std::ceil(span / std::ldexp(1.0, U.wlog));
+    // about 64 tiles per unit (so that a bucket's runs spread over the count
+    // CTA's warps), 4K to 64K wedges each
+    U.tile_w = (int)std::min<long long>(65536, std::max<long long>(4096, (U.W + 63) / 64));
+    U.T = (int)((U.W + U.tile_w - 1) / U.tile_w);
+    U.arc_base = arcs;
+    arcs += (long long)U.kept + 1;
+    wmax = std::max<u64>(wmax, (u64)U.W);
+    S.units[i] = U;
+  }
+  // batches: consecutive units, at most batch_wedges wedges (a larger unit alone)
+  const u64 cap = std::max<u64>((u64)batch_wedges, wmax);
+  for (size_t i = 0; i < S.units.size();) {
+    ExpBatch B{i, i, 0, 0, 0, 0};
+    while (B.u1 < S.units.size() && (B.u1 == B.u0 || B.wedges + S.units[B.u1].W <= cap)) {
+      ExpUnit& U = S.units[B.u1];
+      U.rec_base = (long long)B.wedges;
+      U.tile_base = (long long)B.tiles;
+      U.pre_base = (long long)B.pre;
+      U.bucket_base = (long long)B.buckets;
+      B.wedges += (u64)U.W;
+      B.tiles += (u64)U.T;
+      B.pre += (u64)U.T * (U.nb + 1);
+      B.buckets += (u64)U.nb;
+      ++B.u1;
+    }
+    S.batches.push_back(B);
+    i = B.u1;
+  }
+  XCU(ensure(g, g.s_xunit, sizeof(ExpUnit) * nexp));
+  XCU(ensure(g, g.s_xaseg, sizeof(int) * (size_t)arcs));
+  XCU(ensure(g, g.s_xaoff, sizeof(int) * (size_t)arcs));
+  if (v64) XCU(ensure(g, g.s_xadeg, sizeof(int) * (size_t)arcs));
+  XCU(cudaMemcpyAsync(g.s_xunit.p, S.units.data(), sizeof(ExpUnit) * nexp, cudaMemcpyHostToDevice,
+                      st));
+  if (timing) cudaEventRecord(g.xev[0], st);
+  XCU(launch_exp_arcs(A, sp<ExpUnit>(g.s_xunit), (int)nexp, sp<int>(g.s_xaseg),
+                      sp<int>(g.s_xaoff), v64 ? sp<int>(g.s_xadeg) : nullptr, st));
+  if (timing) cudaEventRecord(g.xev[1], st);
+  S.launches++;
+  // the arc pass checks every unit's wedge count against the estimate
+  u32 err = 0;
+  XCU(cudaMemcpyAsync(&err, &A.ctr->error, sizeof(u32), cudaMemcpyDeviceToHost, st));
+  XCU(cudaStreamSynchronize(st));
+  if (err) return report_error(LP_EINTERNAL, "expand tier: arc pass check failed");
+  if (timing) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, g.xev[0], g.xev[1]) == cudaSuccess) S.ms_expand += ms;
+  }
+  A.xunit = sp<ExpUnit>(g.s_xunit);
+  return LP_OK;
+}
+
+lp_status exp_next_batch(Graph& g, ScanArgs& A, ExpState& S, bool timing,
+                         std::vector<int4>& items) {
+  items.clear();
+  if (S.next >= S.batches.size()) return LP_OK;
+  const ExpBatch B = S.batches[S.next++];
+  cudaStream_t st = g.stream;
+  const bool v64 = A.measure == LP_AA || A.measure == LP_RA;
+  XCU(ensure(g, g.s_xrec, (v64 ? sizeof(int2) : sizeof(int)) * (size_t)B.wedges));
+  XCU(ensure(g, g.s_xtile, sizeof(u64) * (size_t)B.tiles));
+  XCU(ensure(g, g.s_xtunit, sizeof(int) * (size_t)B.tiles));
+  XCU(ensure(g, g.s_xpre, sizeof(int) * (size_t)B.pre));
+  XCU(ensure(g, g.s_xbunit, sizeof(int) * (size_t)B.buckets));
+  std::vector<int> tile_unit(B.tiles), bucket_unit(B.buckets);
+  items.reserve(B.buckets);
+  for (size_t u = B.u0; u < B.u1; ++u) {
+    const ExpUnit& U = S.units[u];
+    for (int t = 0; t < U.T; ++t) tile_unit[U.tile_base + t] = (int)u;
+    for (int b = 0; b < U.nb; ++b) {
+      bucket_unit[U.bucket_base + b] = (int)u;
+      const long long clo = (long long)U.lo + ((long long)b << U.wlog);
+      const long long chi = std::min<long long>(U.hi, clo + (1ll << U.wlog));
+      items.push_back(make_int4(U.a, (int)clo, (int)chi, (int)(U.bucket_base + b) | kExpItem));
+    }
+  }
+  XCU(cudaMemcpyAsync(g.s_xtunit.p, tile_unit.data(), sizeof(int) * B.tiles,
+                      cudaMemcpyHostToDevice, st));
+  XCU(cudaMemcpyAsync(g.s_xbunit.p, bucket_unit.data(), sizeof(int) * B.buckets,
+                      cudaMemcpyHostToDevice, st));
+  if (timing) cudaEventRecord(g.xev[0], st);
+  XCU(launch_exp_tiles(A, sp<ExpUnit>(g.s_xunit), sp<int>(g.s_xtunit), (int)B.tiles,
+                       sp<int>(g.s_xaseg), sp<int>(g.s_xaoff), v64 ? sp<int>(g.s_xadeg) : nullptr,
+                       g.s_xrec.p, sp<u64>(g.s_xtile), sp<int>(g.s_xpre), st));
+  if (timing) cudaEventRecord(g.xev[1], st);
+  S.launches++;
+  // the host vectors must outlive the asynchronous copies
+  XCU(cudaStreamSynchronize(st));
+  if (timing) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, g.xev[0], g.xev[1]) == cudaSuccess) S.ms_expand += ms;
+  }
+  A.xunit = sp<ExpUnit>(g.s_xunit);
+  A.xbucket_unit = sp<int>(g.s_xbunit);
+  A.xrec = g.s_xrec.p;
+  A.xtile_rec = sp<u64>(g.s_xtile);
+  A.xpre = sp<int>(g.s_xpre);
+  return LP_OK;
+}
+
+#undef XCU
+
+}  // namespace lp

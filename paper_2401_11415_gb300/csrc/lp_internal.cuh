@@ -42,6 +42,30 @@ constexpr int kItemSingle = 2;   // the only item of its source (per-source mode
 constexpr int kItemWhole = 4;    // one item covers the source's whole second-order id range
 constexpr int kItemD8 = 8;       // dense, 8-bit counters (global mode, source degree <= 255)
 constexpr int kMaxSweep = 4096;  // windows or ranges of one item (a 12-bit field of the record)
+// Count items of the expand-and-count tier carry this flag in int4.w (the
+// other item kinds leave bit 28 clear) and their batch bucket below it.
+constexpr int kExpItem = 1 << 28;
+constexpr int kExpSplit = 1 << 27;      // a re-split part of a hash bucket
+constexpr int kExpGbMask = kExpSplit - 1;
+constexpr int kExpMaxBuckets = 4096;    // buckets of one unit
+// ExpUnit.flags
+constexpr int kExpDense = 4;            // dense counter windows (else a hash table per bucket)
+constexpr int kExpC8 = 0, kExpC16 = 1, kExpC32 = 2, kExpC64 = 3;  // counter width (flags & 3)
+
+// One source of the expand-and-count large tier (global mode): its wedges
+// are expanded once into records grouped by bucket (an id range of 2^wlog),
+// then each bucket is counted in shared memory.
+struct ExpUnit {
+  int a, lo, hi, kept;   // source, second-order id range [lo, hi), arcs passing the hub test
+  int wlog, nb, flags, tile_w;  // bucket width 2^wlog, buckets, kind, wedges per tile
+  int K, T, pad0, pad1;  // nonempty arc segments (arc pass), tiles
+  long long W;           // wedges
+  long long arc_base;    // first entry of the unit in the segment lists (K + 1 entries)
+  long long rec_base;    // first record of the unit in its batch
+  long long tile_base;   // first tile of the unit in its batch
+  long long pre_base;    // first bucket-start entry of the unit in its batch
+  long long bucket_base; // first batch bucket of the unit
+};
 
 // Arc table entry for arc e = (a -> b): x = position of a in Gamma_b
 // (absolute index into idx), y = off[b + 1], z = |Gamma_b|, w = b.
@@ -84,10 +108,12 @@ struct Counters {
   u64 nsplit;        // overflowed hash items
   u64 npartial;      // per-source partial lists written
   u64 dense_items;
-  u64 tier_wedges[3];
-  u64 tier_arcs[3];
-  u64 tier_kept[3];
+  u64 tier_wedges[4]; // [3]: the expand-and-count tier
+  u64 tier_arcs[4];
+  u64 tier_kept[4];
   u64 prof[6];
+  u64 nexp;          // expand-and-count units written by the estimate kernel
+  u64 claim_x;       // count-item claims
   u32 full;          // selection buffer full
   u32 error;         // device consistency error code
   u64 pad[2];
@@ -146,6 +172,17 @@ struct ScanArgs {
   int item_wedges;     // target wedges of one dense sweep item
   int big_threads;     // threads of a large-tier CTA: 1024 (one per SM) or 512 (two)
   u64* prof;           // optional: large-tier phase cycles (6 entries) or null
+  // expand-and-count tier (global mode)
+  int expand;          // 1: large sources with W > cta_max become units (when W < 2^31)
+  int x_logcap;        // log2 slots of a hash bucket's table
+  int4* xq;            // estimate output: unit records {a, lo, hi, kept}
+  u64* xw;             // and their wedge counts
+  u64 xq_cap;
+  const ExpUnit* xunit;        // units
+  const int* xbucket_unit;     // batch bucket -> unit
+  const void* xrec;            // batch records: int c (count measures) or int2 {c, |Gamma_b|}
+  const u64* xtile_rec;        // batch tile -> first record
+  const int* xpre;             // per tile and bucket: first record within the tile (nb + 1 each)
 };
 
 // Process-wide tuning options (lp_set_option).
@@ -159,6 +196,9 @@ struct Options {
   long long item_wedges = 1 << 18;
   int phase_profile = 0;
   int big_threads = 1024;
+  int expand = 2;                  // 0 off, 1 on, 2 when the index array exceeds 128 MB
+  long long expand_batch = 1ll << 29;  // wedges expanded per batch
+  int expand_logcap = 14;          // log2 slots of the count pass's hash tables
 };
 Options options_snapshot();
 
@@ -184,9 +224,12 @@ struct Graph {
   };
   Scratch s_ctr, s_w, s_warpq, s_itemq, s_warpq2, s_itemq2, s_medq, s_medq2, s_buf, s_buf2,
       s_failed, s_split, s_thresh, s_flags, s_partial, s_phdr, s_top, s_cnt, s_links, s_src, s_grp,
-      s_buf3, s_misc, s_vfloor, s_pair, s_gcur;
+      s_buf3, s_misc, s_vfloor, s_pair, s_gcur, s_xq, s_xw, s_xunit, s_xaseg, s_xaoff, s_xadeg,
+      s_xrec, s_xtile, s_xtunit, s_xpre, s_xbunit, s_countq, s_countq2;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // per kernel
+  cudaEvent_t kev[8] = {nullptr, nullptr, nullptr, nullptr,
+                        nullptr, nullptr, nullptr, nullptr};  // per scan kernel (start, end)
+  cudaEvent_t xev[2] = {nullptr, nullptr};  // expand-and-count passes
 };
 
 // ---------------------------------------------------------------- device --
@@ -221,6 +264,33 @@ cudaError_t launch_count_floor(int measure, int dmax, const Thresh* thresh, u64*
 cudaError_t launch_scan_warp(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
 cudaError_t launch_scan_cta(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
 cudaError_t launch_scan_med(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
+// Expand-and-count tier (lp_expand.cu).
+cudaError_t launch_exp_arcs(const ScanArgs& A, ExpUnit* units, int nunits, int* aseg, int* aoff,
+                            int* adeg, cudaStream_t st);
+cudaError_t launch_exp_tiles(const ScanArgs& A, const ExpUnit* units, const int* tile_unit,
+                             int ntiles, const int* aseg, const int* aoff, const int* adeg,
+                             void* rec, u64* tile_rec, int* pre, cudaStream_t st);
+cudaError_t launch_exp_count(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
+// Host plan of the expand-and-count tier for one global call: the units in
+// batches of at most expand_batch wedges (a larger unit alone).
+struct ExpBatch {
+  size_t u0, u1;               // units [u0, u1)
+  u64 wedges, tiles, pre, buckets;
+};
+struct ExpState {
+  std::vector<ExpUnit> units;
+  std::vector<ExpBatch> batches;
+  size_t next = 0;             // next batch
+  float ms_expand = 0.f;       // device time of the arc and expand passes (timing on)
+  int launches = 0;
+};
+// Read the units the estimate wrote, lay them out and run the arc pass.
+lp_status exp_setup(Graph& g, ScanArgs& A, u64 nexp, long long batch_wedges, bool timing,
+                    ExpState& S);
+// Expand the next batch into A's record buffers; items receives its count
+// items (one per bucket).
+lp_status exp_next_batch(Graph& g, ScanArgs& A, ExpState& S, bool timing,
+                         std::vector<int4>& items);
 cudaError_t launch_build_weights(int dmax, int fixbits, u64* wt, cudaStream_t st);
 cudaError_t launch_estimate2(const ScanArgs& A, int n_rec, int4* warpq, int4* medq, int4* itemq,
                              u64 itemq_cap, int2* grp, cudaStream_t st);

@@ -191,7 +191,7 @@ def test_chunglu4m_per_source_all_vertices(lp, chunglu4m):
         for m in ("JC", "RA"):
             _per_source_check(lp, G, g, m, None, sample, 10, 60, rng)
         st = lp.lp_last_stats()
-        assert all(x > 0 for x in st["tier_launches"])  # every tier ran
+        assert all(x > 0 for x in st["tier_launches"][:3])  # every scan tier ran
 
 
 @pytest.mark.parametrize("measure", ["RA", "AA"])

@@ -190,7 +190,7 @@ def test_split_and_dense_items(lp, big_threads):
                     st = lp.lp_last_stats()
                     if vals[4] == 6 and cap is None:
                         assert st["splits"] > 0 and st["cta_items"] > 0
-                        assert all(x > 0 for x in st["tier_launches"])
+                        assert all(x > 0 for x in st["tier_launches"][:3])
                 src = np.arange(0, g.n, 7, dtype=np.int32)
                 with lp.Graph.from_csr(g) as G:
                     gl, gc = G.predict_sources(m, src, 10, None)
