@@ -16,9 +16,15 @@ e2e:   the same step through the host-buffer API: lp_graph_create from the
 roofline: the dominant scan kernel, algorithmic bytes (Gamma_a ids, degree of
        each b, the b offset of kept arcs, 4 bytes per scanned wedge) / its
        event-timed duration.
+the benchmark spec: the same measurements for R-MAT scale 24 (16,777,216 vertices,
+       10% held out), DLH hub limit 256, JC and RA, N_P = |E^U|.
+cpu_baseline: the CPU oracle on all host cores over the ten calls of the
+       step, run once outside the timed region (plus the cap-16 pair on one
+       thread).
 
 --impl reference runs the CPU oracle (the only reference this method has)
-on a bounded sample of the same workload.
+on a bounded sample of the same workload (the cap-16 JC and RA calls per
+step); our line reports its own edges/s on that sample too (matched_sample).
 """
 from __future__ import annotations
 
@@ -204,21 +210,7 @@ def run_ours(args, rank, world, local_rank):
     # e2e through the host-buffer API (graph upload + host outputs)
     e2e = None if args.no_e2e else run_e2e(lp, torch, obs, k, max(1, min(args.steps, 3)))
 
-    # roofline of the dominant scan kernel
-    tier_ms = [sum(s["tier_ms"][i] for s in stats) for i in range(3)]
-    tier_launch = [sum(s["tier_launches"][i] for s in stats) for i in range(3)]
-    dom = max(range(3), key=lambda i: tier_ms[i])
-    name = ["k_scan_warp", "k_scan_cta", "k_scan_big"][dom]
-    alg_bytes = 0
-    for s in stats:
-        alg_bytes += (4 * s["tier_arcs"][dom] + 4 * s["tier_arcs"][dom] + 4 * s["tier_kept"][dom]
-                      + 4 * s["tier_wedges"][dom])
-    launches = max(1, tier_launch[dom])
-    bytes_per_launch = alg_bytes / launches
-    avg_ms = tier_ms[dom] / launches
-    peak, peak_kind = peaks()
-    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
-    traffic = traffic_record(name)
+    roof = roofline(stats)
     wedges = sum(s["wedges"] for s in stats)
     gpu_launches = sum(s["launches"] for s in stats)
     value = (total * world) / (ms_max / 1e3)
@@ -226,6 +218,10 @@ def run_ours(args, rank, world, local_rank):
     for (m, c), s in zip(calls * args.steps, stats):
         key = f"{m}@{'inf' if c is None else c}"
         per_cap[key] = per_cap.get(key, 0.0) + s["ms_total"]
+    # our rate on the reference arm's sample (the cap-16 JC and RA calls)
+    samp = [f"{m}@{c}" for c, m in SAMPLE_CAPS]
+    samp_ms = sum(per_cap.get(x, 0.0) for x in samp) / args.steps
+    samp_edges = k * len(samp)
     line = {
         "metric": METRIC,
         "value": round(value, 1),
@@ -245,21 +241,110 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}"},
         "e2e": e2e,
         "gpu_launches": int(gpu_launches),
-        "roofline": {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1),
-                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "peak_source": peak_kind, "traffic": traffic,
-                     "alg_bytes_per_launch": int(bytes_per_launch),
-                     "avg_launch_ms": round(avg_ms, 4), "launches": int(launches)},
+        "roofline": roof,
         "wedges_per_s": round(wedges / (ms / 1e3), 1),
         "per_call_ms": {k_: round(v / args.steps, 3) for k_, v in per_cap.items()},
+        "matched_sample": {"calls": samp, "value": round(samp_edges / (samp_ms / 1e3), 1)
+                           if samp_ms > 0 else None, "unit": "edges/s",
+                           "note": "device time of the calls the reference arm times per step"},
         "clocks": clk.summary(),
     }
     if args.scale != 20 or args.only:
         line["config"]["workload"] += f" [subset: scale {args.scale}, calls {args.only or 'all'}]"
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(split)
     G.close()
+    if not args.no_north_star and args.scale == 20 and not args.only:
+        line["north_star"] = run_north_star(lp, torch, args)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(split, args.cpu_baseline)
     return line
+
+
+TIER_KERNELS = ["k_scan_warp", "k_scan_cta", "k_scan_big", "k_exp_tiles+k_exp_count"]
+
+
+def roofline(stats):
+    """The dominant scan kernel (by summed device time): its algorithmic
+    bytes per launch -- 4 B per Gamma_a id and per degree of b over the
+    arcs of the sources binned to it, 4 B per kept arc (the b offset), 4 B
+    per wedge -- over its average event-timed launch.  The expand-and-count
+    tier is one unit here: its time is that of its arc, expand and count
+    passes together, its launches the count-pass launches."""
+    nt = len(stats[0]["tier_ms"]) if stats else 3
+    tier_ms = [sum(s["tier_ms"][i] for s in stats) for i in range(nt)]
+    tier_launch = [sum(s["tier_launches"][i] for s in stats) for i in range(nt)]
+    dom = max(range(nt), key=lambda i: tier_ms[i])
+    name = TIER_KERNELS[dom]
+    alg_bytes = 0
+    for s in stats:
+        alg_bytes += (4 * s["tier_arcs"][dom] + 4 * s["tier_arcs"][dom] + 4 * s["tier_kept"][dom]
+                      + 4 * s["tier_wedges"][dom])
+    launches = max(1, tier_launch[dom])
+    bytes_per_launch = alg_bytes / launches
+    avg_ms = tier_ms[dom] / launches
+    peak, peak_kind = peaks()
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+    return {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+            "traffic": traffic_record(name), "alg_bytes_per_launch": int(bytes_per_launch),
+            "avg_launch_ms": round(avg_ms, 4), "launches": int(launches),
+            "share_of_scan_ms": round(tier_ms[dom] / max(1e-9, sum(tier_ms)), 4)}
+
+
+def run_north_star(lp, torch, args):
+    """R-MAT scale 24 (10% held out), DLH(256) JC and RA with N_P = |E^U|:
+    the configuration the >= 50% HBM target is stated for.  Graph resident,
+    outputs in device memory, CUDA events on the library's stream."""
+    import lp_inputs as L
+    t0 = time.perf_counter()
+    split = L.holdout(L.cfg_rmat24(), 0.1, seed=43)
+    t_gen = time.perf_counter() - t0
+    obs = split.observed
+    k = len(split.hu)
+    G = lp.Graph.from_csr(obs)
+    stream = torch.cuda.ExternalStream(G.stream)
+    d_out = torch.empty((k * 16,), dtype=torch.uint8, device="cuda")
+    calls = [("JC", 256), ("RA", 256)]
+    for _ in range(args.ns_warmup):
+        for m, c in calls:
+            lp.lp_predict_dev(G.handle, m, c, k, 0.0, d_out, k)
+    torch.cuda.synchronize()
+    lp.lp_set_timing(True)
+    stats, total, per = [], 0, {}
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.ns_steps):
+            for m, c in calls:
+                total += lp.lp_predict_dev(G.handle, m, c, k, 0.0, d_out, k)
+                st = lp.lp_last_stats()
+                stats.append(st)
+                per[f"{m}@{c}"] = per.get(f"{m}@{c}", 0.0) + st["ms_total"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    lp.lp_set_timing(False)
+    ms = ev0.elapsed_time(ev1)
+    G.close()
+    # whole-call algorithmic bytes of the survey's formula B_L (every wedge of
+    # every source, 16 B per output link) over the call time
+    b_l = sum(4 * (obs.n + 1) + 8 * obs.arcs + 4 * s["kept_arcs"] + 4 * s["wedges"] + 16 * k
+              for s in stats)
+    peak, peak_kind = peaks()
+    path_gbs = b_l / (ms * 1e-3) / 1e9
+    return {"workload": "R-MAT scale 24 (16,777,216 vertices, edge factor 16, "
+                        "a,b,c=0.57,0.19,0.19), 10% held out; global top-|E^U| for DLH(256) "
+                        "JC and RA",
+            "edges_undirected": int(obs.edges), "N_P": k, "steps": args.ns_steps,
+            "warmup": args.ns_warmup, "ms_per_step": round(ms / args.ns_steps, 3),
+            "ms_per_call": {x: round(v / args.ns_steps, 3) for x, v in per.items()},
+            "edges_per_s": round(total / (ms / 1e3), 1), "unit": "edges/s",
+            "wedges_per_s": round(sum(s["wedges"] for s in stats) / (ms / 1e3), 1),
+            "roofline": roofline(stats),
+            "path_roofline": {"bytes": "B_L of every call (4(N+1) + 8A + 4 kept + 4 W + 16 |P|)",
+                              "achieved": round(path_gbs, 1), "peak": peak, "unit": "GB/s",
+                              "frac": round(path_gbs / peak, 4), "peak_source": peak_kind},
+            "parity": "tests/test_gpu_fullsize.py::test_rmat24_global_sampled",
+            "graph_generate_s": round(t_gen, 1), "clocks": clk.summary()}
 
 
 def run_e2e(lp, torch, obs, k, steps):
@@ -292,14 +377,18 @@ def run_e2e(lp, torch, obs, k, steps):
             "d2h_bytes_per_step": int(16 * total / steps)}
 
 
-def cpu_baseline(split):
+def cpu_baseline(split, which="full"):
+    """The oracle on all host cores, once: over the ten calls of the step
+    ("full", the same work as the timed step) or the cap-16 pair ("sample");
+    and the cap-16 pair on one thread."""
     import oracle
     obs = split.observed
     k = len(split.hu)
     cores = os.cpu_count() or 1
     t = 0.0
     tot = 0
-    for c, m in SAMPLE_CAPS:
+    pairs = [(c, m) for c in CAPS for m in MEASURES] if which == "full" else SAMPLE_CAPS
+    for c, m in pairs:
         t0 = time.perf_counter()
         r = oracle.predict(obs.n, obs.off, obs.idx, m, c, k=k, nthreads=cores)
         t += time.perf_counter() - t0
@@ -310,11 +399,12 @@ def cpu_baseline(split):
         t0 = time.perf_counter()
         n1 += len(oracle.predict(obs.n, obs.off, obs.idx, m, c, k=k, nthreads=1))
         t1 += time.perf_counter() - t0
+    what = ("all ten calls of the step (DLH caps 16, 64, 256, 1024, none x JC, RA), full "
+            "graph, once" if which == "full" else
+            "the DLH cap-16 JC and RA calls of the step, full graph; caps 64-inf left out")
     return {"value": round(tot / t, 1), "unit": "edges/s", "cores": cores,
             "kind": "oracle",
-            "sample": "the DLH cap-16 JC and RA calls of the step, full graph "
-                      f"({tot} predicted edges in {t:.1f} s); caps 64-inf left out to "
-                      "bound the run",
+            "sample": f"{what} ({tot} predicted edges in {t:.1f} s)",
             "one_thread": {"value": round(n1 / t1, 1), "unit": "edges/s", "cores": 1,
                            "sample": f"the same calls on one thread ({n1} predicted edges in "
                                      f"{t1:.1f} s)"}}
@@ -590,6 +680,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-baseline", default="full", choices=["full", "sample"],
+                    help="oracle over all ten calls (full) or the cap-16 pair (sample)")
+    ap.add_argument("--no-north-star", action="store_true",
+                    help="skip the R-MAT scale-24 DLH(256) record")
+    ap.add_argument("--ns-steps", type=int, default=3, help="north_star: timed steps")
+    ap.add_argument("--ns-warmup", type=int, default=1, help="north_star: warm-up steps")
     ap.add_argument("--only", default="", help="subset of calls, e.g. JC@inf,RA@256")
     ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (20 = the workload)")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "serve", "batch"],

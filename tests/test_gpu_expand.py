@@ -50,7 +50,7 @@ def with_options(lp, opts, fn):
             lp.lp_set_option(o, v)
 
 
-def tier_opts(lp, **extra):
+def tier_opts(lp, extra):
     o = {lp.LP_OPT_WARP_MAX_WEDGES: 64, lp.LP_OPT_MED_MAX_WEDGES: 128,
          lp.LP_OPT_CTA_MAX_WEDGES: 257}
     o.update(extra)
@@ -63,12 +63,11 @@ def test_expand_tier_matches_oracle(lp, graph, measure, cap):
     g = graph
     k = 20000
     with lp.Graph.from_csr(g) as G:
-        base = with_options(lp, tier_opts(lp, **{lp.LP_OPT_EXPAND: 0}),
+        base = with_options(lp, tier_opts(lp, {lp.LP_OPT_EXPAND: 0}),
                             lambda: G.predict(measure, cap, k))
-        got = with_options(lp, tier_opts(lp, **{lp.LP_OPT_EXPAND: 1,
-                                                lp.LP_OPT_EXPAND_BATCH: 1 << 16}),
-                           lambda: (G.predict(measure, cap, k), lp.lp_last_stats()))
-        got, st = got
+        got, st = with_options(lp, tier_opts(lp, {lp.LP_OPT_EXPAND: 1,
+                                                  lp.LP_OPT_EXPAND_BATCH: 1 << 16}),
+                               lambda: (G.predict(measure, cap, k), lp.lp_last_stats()))
     assert st["exp_units"] > 0 and st["exp_batches"] > 1 and st["tier_launches"][3] > 0
     assert got.tobytes() == base.tobytes()
     exp = oracle.predict(g.n, g.off, g.idx, measure, cap, k=k)
@@ -84,8 +83,8 @@ def test_expand_tier_overflow_and_compaction(lp, graph, measure):
     k = 20000
     with lp.Graph.from_csr(g) as G:
         base = with_options(lp, {lp.LP_OPT_EXPAND: 0}, lambda: G.predict(measure, None, k))
-        opts = tier_opts(lp, **{lp.LP_OPT_EXPAND: 1, lp.LP_OPT_EXPAND_BATCH: 1 << 17,
-                                lp.LP_OPT_EXPAND_HASH_LOGCAP: 6, lp.LP_OPT_SELECT_BUFFER: 4096})
+        opts = tier_opts(lp, {lp.LP_OPT_EXPAND: 1, lp.LP_OPT_EXPAND_BATCH: 1 << 17,
+                              lp.LP_OPT_EXPAND_HASH_LOGCAP: 6, lp.LP_OPT_SELECT_BUFFER: 4096})
         got, st = with_options(lp, opts, lambda: (G.predict(measure, None, k), lp.lp_last_stats()))
     assert st["exp_units"] > 0 and st["splits"] > 0 and st["compactions"] > 1
     assert got.tobytes() == base.tobytes()
