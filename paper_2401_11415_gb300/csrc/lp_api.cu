@@ -132,7 +132,7 @@ static void free_graph(Graph* g) {
                            &g->s_cnt, &g->s_links, &g->s_src, &g->s_grp, &g->s_xq, &g->s_xw,
                            &g->s_xunit, &g->s_xaseg, &g->s_xaoff, &g->s_xadeg, &g->s_xrec,
                            &g->s_xtile, &g->s_xtunit, &g->s_xpre, &g->s_xbunit, &g->s_countq,
-                           &g->s_countq2};
+                           &g->s_countq2, &g->s_xtfirst, &g->s_xexcl};
   for (auto* s : all)
     if (s->p) cudaFree(s->p);
   if (g->owns_arrays) {
@@ -742,7 +742,8 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
   // the expand-and-count tier pays off where the index array does not stay
   // in the L2 cache (window sweeps then pay DRAM round trips per arc)
   A.expand = opt.expand == 1 || (opt.expand == 2 && g.arcs * (int64_t)sizeof(int) > (128ll << 20));
-  A.x_logcap = opt.expand_logcap;
+  // the count pass's 64 KB table holds 8192 slots of 32-bit values, 4096 of 64-bit
+  A.x_logcap = std::min(opt.expand_logcap, (measure == LP_AA || measure == LP_RA) ? 12 : 13);
   // selection buffer
   const u64 minbuf = (u64)std::max<long long>(16, options_snapshot().select_buffer);
   u64 C = k > 0 ? std::max<u64>(minbuf, 2ull * (u64)k + std::min<u64>(minbuf, 1ull << 20)) : minbuf;

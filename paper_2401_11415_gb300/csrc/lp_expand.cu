@@ -34,8 +34,8 @@
 
 namespace lp {
 
-constexpr int kExpThreads = 256;  // arc and expand passes
-constexpr int kCountThreads = 1024;
+constexpr int kExpThreads = 256;    // arc and expand passes
+constexpr int kCountThreads = 256;  // count pass (three CTAs per SM)
 
 // Exclusive CTA-wide prefix sums of two ints per thread (ex, ey) and their
 // totals.  wsum: 2 * (threads / 32) ints of shared memory; one barrier, and
@@ -81,14 +81,21 @@ __device__ __forceinline__ void exp_scan2(int x, int y, int& ex, int& ey, int& t
 // One CTA per unit: the kept arcs (|Gamma_b| <= L_H) with a nonempty c > a
 // suffix of Gamma_b, compacted: aseg = first index of the suffix in idx, aoff
 // = wedges of the unit before it (aoff[K] = W), adeg = |Gamma_b| (AA / RA).
+// Then the first segment of every tile (tiles of tile_w wedges take the
+// segments that start in them) and, for every bucket, the first entry of
+// Gamma_a at or above the bucket's start (c > a) -- the count pass's
+// first-order exclusion range -- so that neither pass searches.
 __global__ void __launch_bounds__(kExpThreads) k_exp_arcs(ScanArgs A, ExpUnit* __restrict__ units,
                                                            int nunits, int* __restrict__ aseg,
                                                            int* __restrict__ aoff,
-                                                           int* __restrict__ adeg) {
+                                                           int* __restrict__ adeg,
+                                                           int* __restrict__ tfirst,
+                                                           int* __restrict__ excl) {
   __shared__ int wsum[2 * (kExpThreads / 32)];
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const int a = units[u].a;
-    const long long base = units[u].arc_base;
+    const ExpUnit U = units[u];
+    const int a = U.a;
+    const long long base = U.arc_base;
     const int e0 = A.off[a], e1 = A.off[a + 1];
     int carry = 0, cnt = 0;
     for (int eb = e0; eb < e1; eb += kExpThreads) {  // CTA-uniform trips
@@ -119,55 +126,124 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_arcs(ScanArgs A, ExpUnit* _
     if (threadIdx.x == 0) {
       aoff[base + cnt] = carry;
       units[u].K = cnt;
-      if ((long long)carry != units[u].W) atomicExch(&A.ctr->error, 4u);
+      if ((long long)carry != U.W) atomicExch(&A.ctr->error, 4u);
     }
+    __syncthreads();  // this CTA's segment offsets are visible to it
+    // tile t starts at the first segment j with aoff[j] >= t * tile_w:
+    // segment j is the first of the tiles in (aoff[j-1] / tw, aoff[j] / tw]
+    const long long tw = U.tile_w;
+    int* tf = tfirst + U.tfirst_base;
+    for (int j = threadIdx.x; j <= cnt; j += kExpThreads) {
+      long long t0, t1;
+      if (j == 0) {
+        t0 = 0;
+        t1 = 0;
+      } else if (j < cnt) {
+        t0 = (long long)aoff[base + j - 1] / tw + 1;
+        t1 = (long long)aoff[base + j] / tw;
+      } else {  // tiles past the last segment's start: no segment
+        t0 = cnt > 0 ? (long long)aoff[base + cnt - 1] / tw + 1 : 0;
+        t1 = U.T;
+      }
+      for (long long t = t0; t <= t1 && t <= U.T; ++t) tf[t] = j;
+    }
+    // exclusion table: entry b = first index of Gamma_a with value >=
+    // max(a + 1, lo + b 2^wlog) (entry nb: >= hi)
+    int* ex = excl + U.excl_base;
+    for (int b = threadIdx.x; b <= U.nb; b += kExpThreads) {
+      const long long key =
+          b < U.nb ? max((long long)a + 1, (long long)U.lo + ((long long)b << U.wlog)) : U.hi;
+      ex[b] = lower_bound_g(A.idx, e0, e1, (int)min(key, (long long)INT_MAX));
+    }
+    __syncthreads();
   }
 }
 
 // ----------------------------------------------------------- expand pass --
 
-// One CTA per tile: the arcs of the unit whose first wedge lies in
+// The wedges of the warp's 32 segments (lane j: start s_j, length len_j,
+// value w_j), 32 per step, with every lane taking part in every call
+// f(valid, c, w): segments of 64 or more are streamed by the whole warp (four
+// loads in flight per lane), the others concatenated across the lanes.
+template <typename F>
+__device__ __forceinline__ void wedge_stream(int s, int len, int w, const int* __restrict__ idx,
+                                             F&& f) {
+  const int lane = lane_id();
+  u32 lm = __ballot_sync(FULLMASK, len >= kLongArc);
+  while (lm) {
+    const int j = __ffs(lm) - 1;
+    lm &= lm - 1;
+    const int sj = __shfl_sync(FULLMASK, s, j);
+    const int lj = __shfl_sync(FULLMASK, len, j);
+    const int wj = __shfl_sync(FULLMASK, w, j);
+    const int* p = idx + sj;
+    int i = 0;
+    for (; i + 128 <= lj; i += 128) {  // warp-uniform trips
+      const int c0 = __ldg(p + i + lane), c1 = __ldg(p + i + 32 + lane),
+                c2 = __ldg(p + i + 64 + lane), c3 = __ldg(p + i + 96 + lane);
+      f(true, c0, wj);
+      f(true, c1, wj);
+      f(true, c2, wj);
+      f(true, c3, wj);
+    }
+    for (; i < lj; i += 32) {
+      const bool v = i + lane < lj;
+      f(v, v ? __ldg(p + i + lane) : 0, wj);
+    }
+  }
+  if (len >= kLongArc) len = 0;
+  int incl = len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(FULLMASK, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int total = __shfl_sync(FULLMASK, incl, 31);
+  const int excl = incl - len;
+  for (int base = 0; base < total; base += 32) {  // warp-uniform trips
+    const int p0 = base + lane;
+    int j0 = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int e = __shfl_sync(FULLMASK, excl, j0 + step);
+      if (e <= p0) j0 += step;
+    }
+    const int s0 = __shfl_sync(FULLMASK, s, j0) - __shfl_sync(FULLMASK, excl, j0);
+    const int w0 = __shfl_sync(FULLMASK, w, j0);
+    const bool v = p0 < total;
+    f(v, v ? __ldg(idx + s0 + p0) : 0, w0);
+  }
+}
+
+// One CTA per tile: the segments of the unit that start in
 // [tl * tile_w, (tl + 1) * tile_w).  Two passes over their wedges (the
 // second from the cache): a bucket histogram, then every record written to
-// its bucket's slot within the tile.
+// its bucket's slot within the tile.  Lanes of a warp that fall in the same
+// bucket (sorted suffixes put runs of them there) are merged with one
+// match before the shared-memory atomic.
 template <bool V64>
 __global__ void __launch_bounds__(kExpThreads) k_exp_tiles(ScanArgs A, const ExpUnit* __restrict__ units,
                                                            const int* __restrict__ tile_unit,
                                                            int ntiles, const int* __restrict__ aseg,
                                                            const int* __restrict__ aoff,
                                                            const int* __restrict__ adeg,
+                                                           const int* __restrict__ tfirst,
                                                            void* __restrict__ rec,
                                                            u64* __restrict__ tile_rec,
                                                            int* __restrict__ pre) {
   constexpr int NW = kExpThreads / 32;
   __shared__ int hist[kExpMaxBuckets];
   __shared__ int wsum[2 * NW];
-  __shared__ int s_j0, s_j1;
   const int lane = lane_id(), wid = threadIdx.x >> 5;
+  const u32 lt = (1u << lane) - 1u;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int u = tile_unit[t];
     const ExpUnit U = units[u];
     const long long tl = t - U.tile_base;
     const int* off_u = aoff + U.arc_base;
-    if (threadIdx.x == 0) {
-      // first arc starting at or after each tile boundary
-      const long long w0 = tl * U.tile_w, w1 = w0 + U.tile_w;
-      int l = 0, r = U.K;
-      while (l < r) {
-        const int m = (l + r) >> 1;
-        if (off_u[m] < w0) l = m + 1; else r = m;
-      }
-      s_j0 = l;
-      r = U.K;
-      while (l < r) {
-        const int m = (l + r) >> 1;
-        if (off_u[m] < w1) l = m + 1; else r = m;
-      }
-      s_j1 = l;
-    }
+    const int j0 = tfirst[U.tfirst_base + tl], j1 = tfirst[U.tfirst_base + tl + 1];
     for (int b = threadIdx.x; b < U.nb; b += kExpThreads) hist[b] = 0;
     __syncthreads();
-    const int j0 = s_j0, j1 = s_j1;
     const int lo = U.lo, wlog = U.wlog;
     // pass 1: bucket histogram
     for (int jb = j0 + wid * 32; jb < j1; jb += NW * 32) {  // warp-uniform trips
@@ -177,13 +253,17 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_tiles(ScanArgs A, const Exp
         s = aseg[U.arc_base + j];
         len = off_u[j + 1] - off_u[j];
       }
-      scan_arcs<int>(s, len, 0, A.idx, [&](int c, int) { atomicAdd(&hist[(c - lo) >> wlog], 1); });
+      wedge_stream(s, len, 0, A.idx, [&](bool v, int c, int) {
+        const int bk = v ? (c - lo) >> wlog : -1 - lane;
+        const u32 m = __match_any_sync(FULLMASK, bk);
+        if (v && (m & lt) == 0) atomicAdd(&hist[bk], __popc(m));
+      });
     }
     __syncthreads();
     // exclusive prefix of the histogram (each thread a run of buckets); the
     // starts become the write cursors and the tile's bucket-start table
     const int per = (U.nb + kExpThreads - 1) / kExpThreads;
-    const int b0 = min(U.nb, threadIdx.x * per), b1 = min(U.nb, b0 + per);
+    const int b0 = min(U.nb, (int)threadIdx.x * per), b1 = min(U.nb, b0 + per);
     int run = 0;
     for (int b = b0; b < b1; ++b) run += hist[b];
     int ex, ey, tot, tot2;
@@ -195,11 +275,11 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_tiles(ScanArgs A, const Exp
       pt[b] = ex;
       ex += h;
     }
+    const u64 rb = (u64)(U.rec_base + off_u[j0]);
     if (threadIdx.x == 0) {
       pt[U.nb] = tot;
-      tile_rec[t] = (u64)(U.rec_base + (j0 < U.K ? off_u[j0] : off_u[U.K]));
+      tile_rec[t] = rb;
     }
-    const u64 rb = (u64)(U.rec_base + (j0 < U.K ? off_u[j0] : off_u[U.K]));
     __syncthreads();
     // pass 2: every record to its bucket's next slot
     for (int jb = j0 + wid * 32; jb < j1; jb += NW * 32) {  // warp-uniform trips
@@ -210,10 +290,17 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_tiles(ScanArgs A, const Exp
         len = off_u[j + 1] - off_u[j];
         if (V64) db = adeg[U.arc_base + j];
       }
-      scan_arcs<int>(s, len, db, A.idx, [&](int c, int w) {
-        const int pos = atomicAdd(&hist[(c - lo) >> wlog], 1);
-        if (V64) reinterpret_cast<int2*>(rec)[rb + pos] = make_int2(c, w);
-        else reinterpret_cast<int*>(rec)[rb + pos] = c;
+      wedge_stream(s, len, db, A.idx, [&](bool v, int c, int w) {
+        const int bk = v ? (c - lo) >> wlog : -1 - lane;
+        const u32 m = __match_any_sync(FULLMASK, bk);
+        const int leader = __ffs(m) - 1;
+        int pos = 0;
+        if (v && lane == leader) pos = atomicAdd(&hist[bk], __popc(m));
+        pos = __shfl_sync(FULLMASK, pos, leader) + __popc(m & lt);
+        if (v) {
+          if (V64) reinterpret_cast<int2*>(rec)[rb + pos] = make_int2(c, w);
+          else reinterpret_cast<int*>(rec)[rb + pos] = c;
+        }
       });
     }
     __syncthreads();
@@ -222,28 +309,32 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_tiles(ScanArgs A, const Exp
 
 // ------------------------------------------------------------ count pass --
 
-// One CTA per count item {a, clo, chi, batch bucket | kExpItem}: the records
-// of the bucket (from every tile of the unit) with clo <= c < chi are counted
-// in shared memory, the first-order neighbours dropped, and the counters
+// One CTA per count item {a, clo, chi, batch bucket | kExpItem}; three CTAs
+// of kCountThreads per SM (a 64 KB table each) keep several items' memory
+// round trips in flight.  The item's run table (first and last record of the
+// bucket in every tile of the unit) is loaded at once, the records with
+// clo <= c < chi are counted in shared memory, the first-order neighbours in
+// the bucket (from the unit's exclusion table) dropped, and the counters
 // scored and admitted.  A hash item whose table fills is handed back for
 // splitting; a dense item cannot overflow.
-template <bool V64, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1) k_exp_count(ScanArgs A, const int4* __restrict__ q,
-                                                          u64 nq, int table_bytes,
-                                                          u64* __restrict__ claim) {
+template <bool V64>
+__global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, const int4* __restrict__ q,
+                                                                u64 nq, u64* __restrict__ claim) {
   typedef typename std::conditional<V64, u64, u32>::type V;
-  constexpr int NW = THREADS / 32;
-  const int kLogcap = A.x_logcap;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int max_slots = 1 << (ceil_log2((u64)table_bytes / (4 + sizeof(V)) + 1) - 1);
+  constexpr int NW = kCountThreads / 32;
+  constexpr int kSlotsMax = kExpTableBytes / (4 + sizeof(V)) >= 8192 ? 8192 : 4096;
+  const int logcap = A.x_logcap;
+  extern __shared__ __align__(16) unsigned char smem[];  // kExpTableBytes
   int* keys = reinterpret_cast<int*>(smem);
-  V* vals = reinterpret_cast<V*>(smem + (size_t)max_slots * 4);
+  V* vals = reinterpret_cast<V*>(smem + (size_t)kSlotsMax * 4);
   u32* words = reinterpret_cast<u32*>(smem);
+  __shared__ int s_p0[kExpMaxTiles], s_p1[kExpMaxTiles];
+  __shared__ u64 s_rb[kExpMaxTiles];
   __shared__ int4 s_rec;
   __shared__ u64 s_next;
   __shared__ int s_ndistinct, s_overflow, s_fail, s_e0, s_e1;
   const int lane = lane_id(), wid = threadIdx.x >> 5;
-  for (int i = threadIdx.x * 16; i < table_bytes; i += THREADS * 16)
+  for (int i = threadIdx.x * 16; i < kExpTableBytes; i += kCountThreads * 16)
     *reinterpret_cast<int4*>(smem + i) = make_int4(0, 0, 0, 0);
   const Thresh T = *A.thresh;
   u64 n_cand = 0;
@@ -275,10 +366,28 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_count(ScanArgs A, const int4
     const bool dense = (U.flags & kExpDense) != 0;
     const int cw = U.flags & 3;
     const int lg = clo, hg = chi;
-    const int nslots = 1 << kLogcap;
+    const int nslots = 1 << logcap;
     const int limit = (nslots * 3) / 4;
     u32* dlo = words;
     u32* dhi = words + (1 << U.wlog);
+    // the bucket's run in every tile, and its slice of Gamma_a
+    for (int tt = threadIdx.x; tt < U.T; tt += kCountThreads) {
+      const int* pt = A.xpre + U.pre_base + (long long)tt * (U.nb + 1) + b;
+      s_p0[tt] = pt[0];
+      s_p1[tt] = pt[1];
+      s_rb[tt] = A.xtile_rec[U.tile_base + tt];
+    }
+    if (threadIdx.x == 0) {
+      const int* ex = A.xexcl + U.excl_base + b;
+      int e0 = ex[0], e1 = ex[1];
+      if (rec.w & kExpSplit) {  // a part of the bucket: narrow the slice
+        e0 = lower_bound_g(A.idx, e0, e1, max(clo, a + 1));
+        e1 = lower_bound_g(A.idx, e0, e1, chi);
+      }
+      s_e0 = e0;
+      s_e1 = e1;
+    }
+    __syncthreads();
     auto insert = [&](int c, V wc) {
       if (dense) {
         const int p = swz(c - lg);
@@ -296,7 +405,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_count(ScanArgs A, const int4
         }
       } else {
         if (*(volatile int*)&s_overflow) return;
-        const int rc = hash_add<V>(keys, vals, kLogcap, c, wc);
+        const int rc = hash_add<V>(keys, vals, logcap, c, wc);
         if (rc == 1) {
           if (atomicAdd(&s_ndistinct, 1) >= limit) s_overflow = 1;
         } else if (rc == 2) {
@@ -306,10 +415,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_count(ScanArgs A, const int4
     };
     // insert the bucket's records, warps taking the tiles round-robin
     for (int tt = wid; tt < U.T; tt += NW) {  // warp-uniform trips
-      const long long tb = U.tile_base + tt;
-      const int* pt = A.xpre + U.pre_base + (long long)tt * (U.nb + 1) + b;
-      const int p0 = pt[0], p1 = pt[1];
-      const u64 rb = A.xtile_rec[tb];
+      const int p0 = s_p0[tt], p1 = s_p1[tt];
+      const u64 rb = s_rb[tt];
       for (int i = p0 + lane; i < p1; i += 32) {
         int c;
         V w;
@@ -328,7 +435,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_count(ScanArgs A, const int4
     __syncthreads();
     if (!dense && s_overflow) {
       // hand the item back for splitting; leave the table empty
-      for (int i = threadIdx.x * 4; i < nslots; i += THREADS * 4) {
+      for (int i = threadIdx.x * 4; i < nslots; i += kCountThreads * 4) {
         *reinterpret_cast<int4*>(keys + i) = make_int4(0, 0, 0, 0);
         zero4<V>(vals + i);
       }
@@ -341,14 +448,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_count(ScanArgs A, const int4
       continue;
     }
     // drop the first-order neighbours c in [max(clo, a + 1), chi)
-    if (threadIdx.x == 0) {
-      const int e0 = A.off[a], e1 = A.off[a + 1];
-      const int l = lower_bound_g(A.idx, e0, e1, max(clo, a + 1));
-      s_e0 = l;
-      s_e1 = lower_bound_g(A.idx, l, e1, chi);
-    }
-    __syncthreads();
-    for (int e = s_e0 + threadIdx.x; e < s_e1; e += THREADS) {
+    for (int e = s_e0 + threadIdx.x; e < s_e1; e += kCountThreads) {
       const int c = __ldg(A.idx + e);
       if (dense) {
         const int p = swz(c - lg);
@@ -360,7 +460,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_count(ScanArgs A, const int4
           dhi[p] = 0;
         }
       } else {
-        hash_kill<V>(keys, vals, kLogcap, c);
+        hash_kill<V>(keys, vals, logcap, c);
       }
     }
     __syncthreads();
@@ -374,35 +474,35 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_count(ScanArgs A, const int4
     const int npos = (hg - lg + 31) & ~31;
     if (dense && cw == kExpC8) {
       u32 q8 = (u32)qv;
-      for (int base0 = wid * 256; base0 < npos; base0 += THREADS * 8)  // warp-uniform trips
+      for (int base0 = wid * 256; base0 < npos; base0 += kCountThreads * 8)  // warp-uniform
         fail |= score_dense8_linear(A, T, a, da, words, base0, npos, lg, vmin, n_cand, qn, qc, q8,
                                     qd);
       qv = (V)q8;
     } else if (dense && cw == kExpC16) {
       u32 q16 = (u32)qv;
-      for (int base0 = wid * 256; base0 < npos; base0 += THREADS * 8)  // warp-uniform trips
+      for (int base0 = wid * 256; base0 < npos; base0 += kCountThreads * 8)  // warp-uniform
         fail |= score_dense16_linear(A, T, a, da, words, base0, npos, lg, vmin, n_cand, qn, qc,
                                      q16, qd);
       qv = (V)q16;
     } else if (dense && cw == kExpC32) {
       u32 q32 = (u32)qv;
-      for (int base0 = wid * 128; base0 < npos; base0 += THREADS * 4)  // warp-uniform trips
+      for (int base0 = wid * 128; base0 < npos; base0 += kCountThreads * 4)  // warp-uniform
         fail |= score_dense_linear<u32>(A, T, a, da, words, base0, npos, lg, vmin, n_cand, qn, qc,
                                         q32, qd);
       qv = (V)q32;
     } else if (dense) {
       u64 q64 = (u64)qv;
-      for (int base0 = wid * 128; base0 < npos; base0 += THREADS * 4)  // warp-uniform trips
+      for (int base0 = wid * 128; base0 < npos; base0 += kCountThreads * 4)  // warp-uniform
         fail |= score_dense64_linear(A, T, a, da, dlo, dhi, base0, npos, lg, vmin, n_cand, qn, qc,
                                      q64, qd);
       qv = (V)q64;
     } else if (T.valid) {
-      for (int base0 = wid * 128; base0 < nslots; base0 += THREADS * 4)
+      for (int base0 = wid * 128; base0 < nslots; base0 += kCountThreads * 4)
         fail |= score_hash_linear<V>(A, T, a, da, keys, vals, base0, nslots, vmin, n_cand, qn, qc,
                                      qv, qd);
     } else {
       int tcnt = 0;
-      for (int base0 = wid * 128; base0 < nslots; base0 += THREADS * 4)
+      for (int base0 = wid * 128; base0 < nslots; base0 += kCountThreads * 4)
         fail |= score_hash_chunk<V, 0>(A, T, a, da, keys, vals, base0, nslots, nullptr, tcnt,
                                        n_cand);
     }
@@ -424,57 +524,46 @@ __global__ void __launch_bounds__(THREADS, 1) k_exp_count(ScanArgs A, const int4
 
 // ------------------------------------------------------------- launchers --
 
-cudaError_t launch_exp_arcs(const ScanArgs& A, ExpUnit* units, int nunits, int* aseg, int* aoff,
-                            int* adeg, cudaStream_t st) {
-  if (nunits <= 0) return cudaSuccess;
+static int exp_num_sms() {
   int dev = 0, nsm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int blocks = std::min(nunits, nsm * 8);
-  k_exp_arcs<<<blocks, kExpThreads, 0, st>>>(A, units, nunits, aseg, aoff, adeg);
+  return nsm > 0 ? nsm : 1;
+}
+
+cudaError_t launch_exp_arcs(const ScanArgs& A, ExpUnit* units, int nunits, int* aseg, int* aoff,
+                            int* adeg, int* tfirst, int* excl, cudaStream_t st) {
+  if (nunits <= 0) return cudaSuccess;
+  const int blocks = std::min(nunits, exp_num_sms() * 8);
+  k_exp_arcs<<<blocks, kExpThreads, 0, st>>>(A, units, nunits, aseg, aoff, adeg, tfirst, excl);
   return cudaGetLastError();
 }
 
 cudaError_t launch_exp_tiles(const ScanArgs& A, const ExpUnit* units, const int* tile_unit,
                              int ntiles, const int* aseg, const int* aoff, const int* adeg,
-                             void* rec, u64* tile_rec, int* pre, cudaStream_t st) {
+                             const int* tfirst, void* rec, u64* tile_rec, int* pre,
+                             cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
-  int dev = 0, nsm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int blocks = std::min(ntiles, nsm * 6);
+  const int blocks = std::min(ntiles, exp_num_sms() * 8);
   if (A.measure == LP_AA || A.measure == LP_RA)
     k_exp_tiles<true><<<blocks, kExpThreads, 0, st>>>(A, units, tile_unit, ntiles, aseg, aoff,
-                                                       adeg, rec, tile_rec, pre);
+                                                       adeg, tfirst, rec, tile_rec, pre);
   else
     k_exp_tiles<false><<<blocks, kExpThreads, 0, st>>>(A, units, tile_unit, ntiles, aseg, aoff,
-                                                        adeg, rec, tile_rec, pre);
-  return cudaGetLastError();
-}
-
-template <bool V64>
-static cudaError_t launch_count_t(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st) {
-  auto kern = k_exp_count<V64, kCountThreads>;
-  const int tb = kCtaSmem;  // dense windows use 128 KB of it, hash tables up to all
-  cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
-  int dev = 0, optin = 0, nsm = 1;
-  if (e == cudaSuccess) e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin - (int)fa.sharedSizeBytes);
-  if (e != cudaSuccess) return e;
-  const int blocks = (int)std::max<u64>(1, std::min<u64>((u64)nsm, nq));
-  kern<<<blocks, kCountThreads, (size_t)tb, st>>>(A, q, nq, tb, &A.ctr->claim_x);
+                                                        adeg, tfirst, rec, tile_rec, pre);
   return cudaGetLastError();
 }
 
 cudaError_t launch_exp_count(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st) {
   if (nq == 0) return cudaSuccess;
-  if (A.measure == LP_AA || A.measure == LP_RA) return launch_count_t<true>(A, q, nq, st);
-  return launch_count_t<false>(A, q, nq, st);
+  const int blocks = (int)std::max<u64>(1, std::min<u64>((u64)exp_num_sms() * 3, nq));
+  const bool v64 = A.measure == LP_AA || A.measure == LP_RA;
+  auto kern = v64 ? k_exp_count<true> : k_exp_count<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kExpTableBytes);
+  if (e != cudaSuccess) return e;
+  kern<<<blocks, kCountThreads, kExpTableBytes, st>>>(A, q, nq, &A.ctr->claim_x);
+  return cudaGetLastError();
 }
 
 }  // namespace lp
@@ -514,7 +603,7 @@ lp_status exp_setup(Graph& g, ScanArgs& A, u64 nexp, long long batch_wedges, boo
   XCU(cudaStreamSynchronize(st));
   const bool v64 = A.measure == LP_AA || A.measure == LP_RA;
   S.units.resize(nexp);
-  long long arcs = 0;
+  long long arcs = 0, tfirsts = 0, excls = 0;
   u64 wmax = 0;
   for (u64 i = 0; i < nexp; ++i) {
     ExpUnit U;
@@ -526,19 +615,20 @@ lp_status exp_setup(Graph& g, ScanArgs& A, u64 nexp, long long batch_wedges, boo
     U.W = (long long)w[i];
     const double span = (double)std::max(1, U.hi - U.lo);
     // counter width of a dense window: a count never exceeds the kept arcs
+    // (windows fill the count pass's 64 KB table)
     int cw, wd;
     if (v64) {
       cw = kExpC64;
-      wd = 14;
+      wd = 13;
     } else if (U.kept <= 255) {
       cw = kExpC8;
-      wd = 17;
+      wd = 16;
     } else if (U.kept <= 65535) {
       cw = kExpC16;
-      wd = 16;
+      wd = 15;
     } else {
       cw = kExpC32;
-      wd = 15;
+      wd = 14;
     }
     const double nb_dense = std::ceil(span / std::ldexp(1.0, wd));
     const double per_window = (double)U.W * std::ldexp(1.0, wd) / span;
@@ -547,17 +637,21 @@ lp_status exp_setup(Graph& g, ScanArgs& A, u64 nexp, long long batch_wedges, boo
       U.wlog = wd;
     } else {
       U.flags = cw;
-      const double per_bucket = std::ldexp(1.0, A.x_logcap - 1);
+      const double per_bucket = std::ldexp(1.0, A.x_logcap - 1);  // half the table
       U.wlog = std::max(0, floor_log2(per_bucket * span / (double)std::max<long long>(1, U.W)));
       while (std::ceil(span / std::ldexp(1.0, U.wlog)) > kExpMaxBuckets) ++U.wlog;
     }
     U.nb = (int)std::ceil(span / std::ldexp(1.0, U.wlog));
-    // about 64 tiles per unit (so that a bucket's runs spread over the count
-    // CTA's warps), 4K to 64K wedges each
-    U.tile_w = (int)std::min<long long>(65536, std::max<long long>(4096, (U.W + 63) / 64));
+    // tiles of at least 4K wedges, at most kExpMaxTiles per unit (the count
+    // pass loads a bucket's runs of every tile at once)
+    U.tile_w = (int)std::max<long long>(4096, (U.W + kExpMaxTiles - 1) / kExpMaxTiles);
     U.T = (int)((U.W + U.tile_w - 1) / U.tile_w);
     U.arc_base = arcs;
     arcs += (long long)U.kept + 1;
+    U.tfirst_base = tfirsts;
+    tfirsts += (long long)U.T + 1;
+    U.excl_base = excls;
+    excls += (long long)U.nb + 1;
     wmax = std::max<u64>(wmax, (u64)U.W);
     S.units[i] = U;
   }
@@ -584,11 +678,14 @@ lp_status exp_setup(Graph& g, ScanArgs& A, u64 nexp, long long batch_wedges, boo
   XCU(ensure(g, g.s_xaseg, sizeof(int) * (size_t)arcs));
   XCU(ensure(g, g.s_xaoff, sizeof(int) * (size_t)arcs));
   if (v64) XCU(ensure(g, g.s_xadeg, sizeof(int) * (size_t)arcs));
+  XCU(ensure(g, g.s_xtfirst, sizeof(int) * (size_t)tfirsts));
+  XCU(ensure(g, g.s_xexcl, sizeof(int) * (size_t)excls));
   XCU(cudaMemcpyAsync(g.s_xunit.p, S.units.data(), sizeof(ExpUnit) * nexp, cudaMemcpyHostToDevice,
                       st));
   if (timing) cudaEventRecord(g.xev[0], st);
   XCU(launch_exp_arcs(A, sp<ExpUnit>(g.s_xunit), (int)nexp, sp<int>(g.s_xaseg),
-                      sp<int>(g.s_xaoff), v64 ? sp<int>(g.s_xadeg) : nullptr, st));
+                      sp<int>(g.s_xaoff), v64 ? sp<int>(g.s_xadeg) : nullptr,
+                      sp<int>(g.s_xtfirst), sp<int>(g.s_xexcl), st));
   if (timing) cudaEventRecord(g.xev[1], st);
   S.launches++;
   // the arc pass checks every unit's wedge count against the estimate
@@ -601,6 +698,7 @@ lp_status exp_setup(Graph& g, ScanArgs& A, u64 nexp, long long batch_wedges, boo
     if (cudaEventElapsedTime(&ms, g.xev[0], g.xev[1]) == cudaSuccess) S.ms_expand += ms;
   }
   A.xunit = sp<ExpUnit>(g.s_xunit);
+  A.xexcl = sp<int>(g.s_xexcl);
   return LP_OK;
 }
 
@@ -635,7 +733,8 @@ lp_status exp_next_batch(Graph& g, ScanArgs& A, ExpState& S, bool timing,
   if (timing) cudaEventRecord(g.xev[0], st);
   XCU(launch_exp_tiles(A, sp<ExpUnit>(g.s_xunit), sp<int>(g.s_xtunit), (int)B.tiles,
                        sp<int>(g.s_xaseg), sp<int>(g.s_xaoff), v64 ? sp<int>(g.s_xadeg) : nullptr,
-                       g.s_xrec.p, sp<u64>(g.s_xtile), sp<int>(g.s_xpre), st));
+                       sp<int>(g.s_xtfirst), g.s_xrec.p, sp<u64>(g.s_xtile), sp<int>(g.s_xpre),
+                       st));
   if (timing) cudaEventRecord(g.xev[1], st);
   S.launches++;
   // the host vectors must outlive the asynchronous copies
@@ -649,6 +748,7 @@ lp_status exp_next_batch(Graph& g, ScanArgs& A, ExpState& S, bool timing,
   A.xrec = g.s_xrec.p;
   A.xtile_rec = sp<u64>(g.s_xtile);
   A.xpre = sp<int>(g.s_xpre);
+  A.xexcl = sp<int>(g.s_xexcl);
   return LP_OK;
 }
 

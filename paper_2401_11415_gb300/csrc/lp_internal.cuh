@@ -48,6 +48,8 @@ constexpr int kExpItem = 1 << 28;
 constexpr int kExpSplit = 1 << 27;      // a re-split part of a hash bucket
 constexpr int kExpGbMask = kExpSplit - 1;
 constexpr int kExpMaxBuckets = 4096;    // buckets of one unit
+constexpr int kExpMaxTiles = 256;       // tiles of one unit
+constexpr int kExpTableBytes = 64 * 1024;  // count pass: table of one CTA (three per SM)
 // ExpUnit.flags
 constexpr int kExpDense = 4;            // dense counter windows (else a hash table per bucket)
 constexpr int kExpC8 = 0, kExpC16 = 1, kExpC32 = 2, kExpC64 = 3;  // counter width (flags & 3)
@@ -58,9 +60,12 @@ constexpr int kExpC8 = 0, kExpC16 = 1, kExpC32 = 2, kExpC64 = 3;  // counter wid
 struct ExpUnit {
   int a, lo, hi, kept;   // source, second-order id range [lo, hi), arcs passing the hub test
   int wlog, nb, flags, tile_w;  // bucket width 2^wlog, buckets, kind, wedges per tile
-  int K, T, pad0, pad1;  // nonempty arc segments (arc pass), tiles
+  int K, T, pad0, pad1;  // nonempty arc segments (arc pass), tiles (at most kExpMaxTiles)
   long long W;           // wedges
   long long arc_base;    // first entry of the unit in the segment lists (K + 1 entries)
+  long long tfirst_base; // first entry of the unit's tile table (T + 1: first segment of each tile)
+  long long excl_base;   // first entry of the unit's exclusion table (nb + 1: first index of
+                         // Gamma_a at or above each bucket start)
   long long rec_base;    // first record of the unit in its batch
   long long tile_base;   // first tile of the unit in its batch
   long long pre_base;    // first bucket-start entry of the unit in its batch
@@ -183,6 +188,7 @@ struct ScanArgs {
   const void* xrec;            // batch records: int c (count measures) or int2 {c, |Gamma_b|}
   const u64* xtile_rec;        // batch tile -> first record
   const int* xpre;             // per tile and bucket: first record within the tile (nb + 1 each)
+  const int* xexcl;            // per unit and bucket: first index of Gamma_a in the bucket
 };
 
 // Process-wide tuning options (lp_set_option).
@@ -225,7 +231,7 @@ struct Graph {
   Scratch s_ctr, s_w, s_warpq, s_itemq, s_warpq2, s_itemq2, s_medq, s_medq2, s_buf, s_buf2,
       s_failed, s_split, s_thresh, s_flags, s_partial, s_phdr, s_top, s_cnt, s_links, s_src, s_grp,
       s_buf3, s_misc, s_vfloor, s_pair, s_gcur, s_xq, s_xw, s_xunit, s_xaseg, s_xaoff, s_xadeg,
-      s_xrec, s_xtile, s_xtunit, s_xpre, s_xbunit, s_countq, s_countq2;
+      s_xrec, s_xtile, s_xtunit, s_xpre, s_xbunit, s_countq, s_countq2, s_xtfirst, s_xexcl;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t kev[8] = {nullptr, nullptr, nullptr, nullptr,
                         nullptr, nullptr, nullptr, nullptr};  // per scan kernel (start, end)
@@ -266,10 +272,11 @@ cudaError_t launch_scan_cta(const ScanArgs& A, const int4* q, u64 nq, cudaStream
 cudaError_t launch_scan_med(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
 // Expand-and-count tier (lp_expand.cu).
 cudaError_t launch_exp_arcs(const ScanArgs& A, ExpUnit* units, int nunits, int* aseg, int* aoff,
-                            int* adeg, cudaStream_t st);
+                            int* adeg, int* tfirst, int* excl, cudaStream_t st);
 cudaError_t launch_exp_tiles(const ScanArgs& A, const ExpUnit* units, const int* tile_unit,
                              int ntiles, const int* aseg, const int* aoff, const int* adeg,
-                             void* rec, u64* tile_rec, int* pre, cudaStream_t st);
+                             const int* tfirst, void* rec, u64* tile_rec, int* pre,
+                             cudaStream_t st);
 cudaError_t launch_exp_count(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
 // Host plan of the expand-and-count tier for one global call: the units in
 // batches of at most expand_batch wedges (a larger unit alone).

@@ -50,3 +50,21 @@ def test_traffic_record_follows_kernel_hash(tmp_path, monkeypatch):
     assert b.traffic_record("k_scan_cta") is None
     monkeypatch.setattr(b, "kernel_hash", lambda: "0" * 16)
     assert b.traffic_record("k_scan_big") is None
+
+
+def test_roofline_picks_dominant_tier_and_counts_its_bytes():
+    b = _bench_module()
+    st = {"tier_ms": [1.0, 2.0, 3.0, 10.0], "tier_launches": [1, 1, 2, 4],
+          "tier_arcs": [10, 20, 30, 1000], "tier_kept": [5, 5, 5, 500],
+          "tier_wedges": [7, 7, 7, 100000]}
+    r = b.roofline([st, st])
+    assert r["kernel"] == "k_exp_tiles+k_exp_count"
+    alg = 2 * (8 * 1000 + 4 * 500 + 4 * 100000)
+    assert r["launches"] == 8 and r["alg_bytes_per_launch"] == alg // 8
+    assert abs(r["avg_launch_ms"] - 20.0 / 8) < 1e-9
+    gbs = (alg / 8) / (20.0 / 8 * 1e-3) / 1e9
+    assert abs(r["achieved"] - round(gbs, 1)) < 0.11
+    assert abs(r["frac"] - round(gbs / r["peak"], 4)) < 1e-4
+    assert abs(r["share_of_scan_ms"] - 10.0 / 16.0) < 1e-4
+    old = {k: v[:3] for k, v in st.items()}  # three tiers (per-source statistics)
+    assert b.roofline([old])["kernel"] == "k_scan_big"
