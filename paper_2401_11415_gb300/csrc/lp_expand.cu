@@ -147,13 +147,20 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_arcs(ScanArgs A, ExpUnit* _
       }
       for (long long t = t0; t <= t1 && t <= U.T; ++t) tf[t] = j;
     }
-    // exclusion table: entry b = first index of Gamma_a with value >=
-    // max(a + 1, lo + b 2^wlog) (entry nb: >= hi)
+    // exclusion table: entry b = first index of Gamma_a with value >= the
+    // bucket's start lo + b 2^wlog (entry nb: >= hi); lo > a, so these are
+    // first-order neighbours above a.  With g(x) the number of starts <= x,
+    // entry e of Gamma_a begins the entries b in [g(Gamma_a[e-1]), g(Gamma_a[e])):
+    // one pass over Gamma_a, no search.
     int* ex = excl + U.excl_base;
-    for (int b = threadIdx.x; b <= U.nb; b += kExpThreads) {
-      const long long key =
-          b < U.nb ? max((long long)a + 1, (long long)U.lo + ((long long)b << U.wlog)) : U.hi;
-      ex[b] = lower_bound_g(A.idx, e0, e1, (int)min(key, (long long)INT_MAX));
+    const int lo = U.lo, hi = U.hi, nb = U.nb, wlog = U.wlog;
+    auto starts_le = [&](int x) {
+      return x < lo ? 0 : (x >= hi ? nb + 1 : ((x - lo) >> wlog) + 1);
+    };
+    for (int e = e0 + threadIdx.x; e <= e1; e += kExpThreads) {
+      const int gp = e > e0 ? starts_le(__ldg(A.idx + e - 1)) : 0;
+      const int gc = e < e1 ? starts_le(__ldg(A.idx + e)) : nb + 1;
+      for (int b = gp; b < gc; ++b) ex[b] = e;
     }
     __syncthreads();
   }
@@ -161,66 +168,10 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_arcs(ScanArgs A, ExpUnit* _
 
 // ----------------------------------------------------------- expand pass --
 
-// The wedges of the warp's 32 segments (lane j: start s_j, length len_j,
-// value w_j), 32 per step, with every lane taking part in every call
-// f(valid, c, w): segments of 64 or more are streamed by the whole warp (four
-// loads in flight per lane), the others concatenated across the lanes.
-template <typename F>
-__device__ __forceinline__ void wedge_stream(int s, int len, int w, const int* __restrict__ idx,
-                                             F&& f) {
-  const int lane = lane_id();
-  u32 lm = __ballot_sync(FULLMASK, len >= kLongArc);
-  while (lm) {
-    const int j = __ffs(lm) - 1;
-    lm &= lm - 1;
-    const int sj = __shfl_sync(FULLMASK, s, j);
-    const int lj = __shfl_sync(FULLMASK, len, j);
-    const int wj = __shfl_sync(FULLMASK, w, j);
-    const int* p = idx + sj;
-    int i = 0;
-    for (; i + 128 <= lj; i += 128) {  // warp-uniform trips
-      const int c0 = __ldg(p + i + lane), c1 = __ldg(p + i + 32 + lane),
-                c2 = __ldg(p + i + 64 + lane), c3 = __ldg(p + i + 96 + lane);
-      f(true, c0, wj);
-      f(true, c1, wj);
-      f(true, c2, wj);
-      f(true, c3, wj);
-    }
-    for (; i < lj; i += 32) {
-      const bool v = i + lane < lj;
-      f(v, v ? __ldg(p + i + lane) : 0, wj);
-    }
-  }
-  if (len >= kLongArc) len = 0;
-  int incl = len;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(FULLMASK, incl, o);
-    if (lane >= o) incl += t;
-  }
-  const int total = __shfl_sync(FULLMASK, incl, 31);
-  const int excl = incl - len;
-  for (int base = 0; base < total; base += 32) {  // warp-uniform trips
-    const int p0 = base + lane;
-    int j0 = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const int e = __shfl_sync(FULLMASK, excl, j0 + step);
-      if (e <= p0) j0 += step;
-    }
-    const int s0 = __shfl_sync(FULLMASK, s, j0) - __shfl_sync(FULLMASK, excl, j0);
-    const int w0 = __shfl_sync(FULLMASK, w, j0);
-    const bool v = p0 < total;
-    f(v, v ? __ldg(idx + s0 + p0) : 0, w0);
-  }
-}
-
 // One CTA per tile: the segments of the unit that start in
 // [tl * tile_w, (tl + 1) * tile_w).  Two passes over their wedges (the
 // second from the cache): a bucket histogram, then every record written to
-// its bucket's slot within the tile.  Lanes of a warp that fall in the same
-// bucket (sorted suffixes put runs of them there) are merged with one
-// match before the shared-memory atomic.
+// its bucket's slot within the tile.
 template <bool V64>
 __global__ void __launch_bounds__(kExpThreads) k_exp_tiles(ScanArgs A, const ExpUnit* __restrict__ units,
                                                            const int* __restrict__ tile_unit,
@@ -235,7 +186,6 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_tiles(ScanArgs A, const Exp
   __shared__ int hist[kExpMaxBuckets];
   __shared__ int wsum[2 * NW];
   const int lane = lane_id(), wid = threadIdx.x >> 5;
-  const u32 lt = (1u << lane) - 1u;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int u = tile_unit[t];
     const ExpUnit U = units[u];
@@ -253,11 +203,7 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_tiles(ScanArgs A, const Exp
         s = aseg[U.arc_base + j];
         len = off_u[j + 1] - off_u[j];
       }
-      wedge_stream(s, len, 0, A.idx, [&](bool v, int c, int) {
-        const int bk = v ? (c - lo) >> wlog : -1 - lane;
-        const u32 m = __match_any_sync(FULLMASK, bk);
-        if (v && (m & lt) == 0) atomicAdd(&hist[bk], __popc(m));
-      });
+      scan_arcs<int>(s, len, 0, A.idx, [&](int c, int) { atomicAdd(&hist[(c - lo) >> wlog], 1); });
     }
     __syncthreads();
     // exclusive prefix of the histogram (each thread a run of buckets); the
@@ -290,17 +236,10 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_tiles(ScanArgs A, const Exp
         len = off_u[j + 1] - off_u[j];
         if (V64) db = adeg[U.arc_base + j];
       }
-      wedge_stream(s, len, db, A.idx, [&](bool v, int c, int w) {
-        const int bk = v ? (c - lo) >> wlog : -1 - lane;
-        const u32 m = __match_any_sync(FULLMASK, bk);
-        const int leader = __ffs(m) - 1;
-        int pos = 0;
-        if (v && lane == leader) pos = atomicAdd(&hist[bk], __popc(m));
-        pos = __shfl_sync(FULLMASK, pos, leader) + __popc(m & lt);
-        if (v) {
-          if (V64) reinterpret_cast<int2*>(rec)[rb + pos] = make_int2(c, w);
-          else reinterpret_cast<int*>(rec)[rb + pos] = c;
-        }
+      scan_arcs<int>(s, len, db, A.idx, [&](int c, int w) {
+        const int pos = atomicAdd(&hist[(c - lo) >> wlog], 1);
+        if (V64) reinterpret_cast<int2*>(rec)[rb + pos] = make_int2(c, w);
+        else reinterpret_cast<int*>(rec)[rb + pos] = c;
       });
     }
     __syncthreads();
