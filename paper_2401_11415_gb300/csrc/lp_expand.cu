@@ -35,6 +35,7 @@
 namespace lp {
 
 constexpr int kExpThreads = 256;    // arc and expand passes
+constexpr int kSub = kExpThreads / 32;  // a tile's sub-tiles: one per warp of the expand CTA
 constexpr int kCountThreads = 256;  // count pass (three CTAs per SM)
 
 // Exclusive CTA-wide prefix sums of two ints per thread (ex, ey) and their
@@ -81,8 +82,9 @@ __device__ __forceinline__ void exp_scan2(int x, int y, int& ex, int& ey, int& t
 // One CTA per unit: the kept arcs (|Gamma_b| <= L_H) with a nonempty c > a
 // suffix of Gamma_b, compacted: aseg = first index of the suffix in idx, aoff
 // = wedges of the unit before it (aoff[K] = W), adeg = |Gamma_b| (AA / RA).
-// Then the first segment of every tile (tiles of tile_w wedges take the
-// segments that start in them) and, for every bucket, the first entry of
+// Then the first segment of every sub-tile (tiles of tile_w wedges, cut into
+// kSub sub-tiles of tile_w / kSub, take the segments that start in them)
+// and, for every bucket, the first entry of
 // Gamma_a at or above the bucket's start (c > a) -- the count pass's
 // first-order exclusion range -- so that neither pass searches.
 __global__ void __launch_bounds__(kExpThreads) k_exp_arcs(ScanArgs A, ExpUnit* __restrict__ units,
@@ -129,9 +131,10 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_arcs(ScanArgs A, ExpUnit* _
       if ((long long)carry != U.W) atomicExch(&A.ctr->error, 4u);
     }
     __syncthreads();  // this CTA's segment offsets are visible to it
-    // tile t starts at the first segment j with aoff[j] >= t * tile_w:
-    // segment j is the first of the tiles in (aoff[j-1] / tw, aoff[j] / tw]
-    const long long tw = U.tile_w;
+    // sub-tile t starts at the first segment j with aoff[j] >= t * sw:
+    // segment j is the first of the sub-tiles in (aoff[j-1] / sw, aoff[j] / sw]
+    const long long tw = U.tile_w / kSub;
+    const long long nsub = (long long)U.T * kSub;
     int* tf = tfirst + U.tfirst_base;
     for (int j = threadIdx.x; j <= cnt; j += kExpThreads) {
       long long t0, t1;
@@ -141,11 +144,11 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_arcs(ScanArgs A, ExpUnit* _
       } else if (j < cnt) {
         t0 = (long long)aoff[base + j - 1] / tw + 1;
         t1 = (long long)aoff[base + j] / tw;
-      } else {  // tiles past the last segment's start: no segment
+      } else {  // sub-tiles past the last segment's start: no segment
         t0 = cnt > 0 ? (long long)aoff[base + cnt - 1] / tw + 1 : 0;
-        t1 = U.T;
+        t1 = nsub;
       }
-      for (long long t = t0; t <= t1 && t <= U.T; ++t) tf[t] = j;
+      for (long long t = t0; t <= t1 && t <= nsub; ++t) tf[t] = j;
     }
     // exclusion table: entry b = first index of Gamma_a with value >= the
     // bucket's start lo + b 2^wlog (entry nb: >= hi); lo > a, so these are
@@ -169,9 +172,10 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_arcs(ScanArgs A, ExpUnit* _
 // ----------------------------------------------------------- expand pass --
 
 // One CTA per tile: the segments of the unit that start in
-// [tl * tile_w, (tl + 1) * tile_w).  Two passes over their wedges (the
-// second from the cache): a bucket histogram, then every record written to
-// its bucket's slot within the tile.
+// [tl * tile_w, (tl + 1) * tile_w), each warp those of one sub-tile (about
+// tile_w / kSub wedges, so the warps reach the barriers together).  Two
+// passes over their wedges (the second from the cache): a bucket histogram,
+// then every record written to its bucket's slot within the tile.
 template <bool V64>
 __global__ void __launch_bounds__(kExpThreads) k_exp_tiles(ScanArgs A, const ExpUnit* __restrict__ units,
                                                            const int* __restrict__ tile_unit,
@@ -191,15 +195,17 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_tiles(ScanArgs A, const Exp
     const ExpUnit U = units[u];
     const long long tl = t - U.tile_base;
     const int* off_u = aoff + U.arc_base;
-    const int j0 = tfirst[U.tfirst_base + tl], j1 = tfirst[U.tfirst_base + tl + 1];
+    const int* tf = tfirst + U.tfirst_base + tl * kSub;
+    const int j0 = tf[0];                    // the tile's first segment
+    const int jw0 = tf[wid], jw1 = tf[wid + 1];  // this warp's sub-tile
     for (int b = threadIdx.x; b < U.nb; b += kExpThreads) hist[b] = 0;
     __syncthreads();
     const int lo = U.lo, wlog = U.wlog;
     // pass 1: bucket histogram
-    for (int jb = j0 + wid * 32; jb < j1; jb += NW * 32) {  // warp-uniform trips
+    for (int jb = jw0; jb < jw1; jb += 32) {  // warp-uniform trips
       const int j = jb + lane;
       int s = 0, len = 0;
-      if (j < j1) {
+      if (j < jw1) {
         s = aseg[U.arc_base + j];
         len = off_u[j + 1] - off_u[j];
       }
@@ -228,10 +234,10 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_tiles(ScanArgs A, const Exp
     }
     __syncthreads();
     // pass 2: every record to its bucket's next slot
-    for (int jb = j0 + wid * 32; jb < j1; jb += NW * 32) {  // warp-uniform trips
+    for (int jb = jw0; jb < jw1; jb += 32) {  // warp-uniform trips
       const int j = jb + lane;
       int s = 0, len = 0, db = 0;
-      if (j < j1) {
+      if (j < jw1) {
         s = aseg[U.arc_base + j];
         len = off_u[j + 1] - off_u[j];
         if (V64) db = adeg[U.arc_base + j];
@@ -249,13 +255,15 @@ __global__ void __launch_bounds__(kExpThreads) k_exp_tiles(ScanArgs A, const Exp
 // ------------------------------------------------------------ count pass --
 
 // One CTA per count item {a, clo, chi, batch bucket | kExpItem}; three CTAs
-// of kCountThreads per SM (a 64 KB table each) keep several items' memory
-// round trips in flight.  The item's run table (first and last record of the
-// bucket in every tile of the unit) is loaded at once, the records with
-// clo <= c < chi are counted in shared memory, the first-order neighbours in
-// the bucket (from the unit's exclusion table) dropped, and the counters
-// scored and admitted.  A hash item whose table fills is handed back for
-// splitting; a dense item cannot overflow.
+// of kCountThreads per SM (a 64 KB table each).  Per item: the run table (the
+// bucket's first and last record in every tile of the unit) and the slice of
+// Gamma_a in the bucket are loaded at once; the records with clo <= c < chi
+// are counted in shared memory, each warp taking an equal share of them in
+// the order of the runs; the first-order neighbours are dropped; and the
+// counters are scored and admitted.  The next item's record and unit are
+// fetched by thread 0 while the current one is counted, so its chain of
+// dependent loads overlaps the work.  A hash item whose table fills is handed
+// back for splitting; a dense item cannot overflow.
 template <bool V64>
 __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, const int4* __restrict__ q,
                                                                 u64 nq, u64* __restrict__ claim) {
@@ -267,9 +275,12 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
   int* keys = reinterpret_cast<int*>(smem);
   V* vals = reinterpret_cast<V*>(smem + (size_t)kSlotsMax * 4);
   u32* words = reinterpret_cast<u32*>(smem);
-  __shared__ int s_p0[kExpMaxTiles], s_p1[kExpMaxTiles];
-  __shared__ u64 s_rb[kExpMaxTiles];
-  __shared__ int4 s_rec;
+  __shared__ int s_p0[kExpMaxTiles];       // run start within its tile
+  __shared__ int s_pre[kExpMaxTiles + 1];  // records before the run (flattened order)
+  __shared__ u64 s_rb[kExpMaxTiles];       // the tile's first record
+  __shared__ int2 s_wsum[NW];
+  __shared__ int4 s_rec, s_rec_next;
+  __shared__ ExpUnit s_unit, s_unit_next;
   __shared__ u64 s_next;
   __shared__ int s_ndistinct, s_overflow, s_fail, s_e0, s_e1;
   const int lane = lane_id(), wid = threadIdx.x >> 5;
@@ -277,56 +288,87 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
     *reinterpret_cast<int4*>(smem + i) = make_int4(0, 0, 0, 0);
   const Thresh T = *A.thresh;
   u64 n_cand = 0;
+  // claim and fetch (record, unit) of an item; thread 0 only
+  auto fetch = [&](u64 qi, int4& r, ExpUnit& U) {
+    if (qi < nq) {
+      r = q[qi];
+      U = A.xunit[A.xbucket_unit[r.w & kExpGbMask]];
+    }
+  };
   if (threadIdx.x == 0) {
-    if (*(volatile u32*)&A.ctr->full) s_next = ~0ull;
-    else s_next = atomicAdd(claim, 1ull);
+    s_next = *(volatile u32*)&A.ctr->full ? ~0ull : atomicAdd(claim, 1ull);
+    fetch(s_next, s_rec_next, s_unit_next);
   }
   __syncthreads();
   for (;;) {
     const u64 qi = s_next;
     if (qi >= nq) break;
     if (threadIdx.x == 0) {
-      s_rec = q[qi];
+      s_rec = s_rec_next;
+      s_unit = s_unit_next;
       s_fail = 0;
       s_ndistinct = 0;
       s_overflow = 0;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {  // look-ahead claim, read after the item
-      if (*(volatile u32*)&A.ctr->full) s_next = ~0ull;
-      else s_next = atomicAdd(claim, 1ull);
-    }
     const int4 rec = s_rec;
+    const ExpUnit& U = s_unit;
     const int a = rec.x, clo = rec.y, chi = rec.z;
     const int gb = rec.w & kExpGbMask;
-    const int u = A.xbucket_unit[gb];
-    const ExpUnit U = A.xunit[u];
     const int b = (int)(gb - U.bucket_base);
     const bool dense = (U.flags & kExpDense) != 0;
     const int cw = U.flags & 3;
+    const int wlog = U.wlog, nt = U.T;
     const int lg = clo, hg = chi;
     const int nslots = 1 << logcap;
     const int limit = (nslots * 3) / 4;
     u32* dlo = words;
-    u32* dhi = words + (1 << U.wlog);
-    // the bucket's run in every tile, and its slice of Gamma_a
-    for (int tt = threadIdx.x; tt < U.T; tt += kCountThreads) {
-      const int* pt = A.xpre + U.pre_base + (long long)tt * (U.nb + 1) + b;
-      s_p0[tt] = pt[0];
-      s_p1[tt] = pt[1];
-      s_rb[tt] = A.xtile_rec[U.tile_base + tt];
-    }
-    if (threadIdx.x == 0) {
-      const int* ex = A.xexcl + U.excl_base + b;
-      int e0 = ex[0], e1 = ex[1];
-      if (rec.w & kExpSplit) {  // a part of the bucket: narrow the slice
-        e0 = lower_bound_g(A.idx, e0, e1, max(clo, a + 1));
-        e1 = lower_bound_g(A.idx, e0, e1, chi);
+    u32* dhi = words + (1 << wlog);
+    // the bucket's run in every tile (one per thread) and their prefix; the
+    // slice of Gamma_a in the bucket
+    {
+      int len = 0;
+      const int tt = threadIdx.x;
+      if (tt < nt) {
+        const int* pt = A.xpre + U.pre_base + (long long)tt * (U.nb + 1) + b;
+        const int p0 = pt[0];
+        len = pt[1] - p0;
+        s_p0[tt] = p0;
+        s_rb[tt] = A.xtile_rec[U.tile_base + tt];
       }
-      s_e0 = e0;
-      s_e1 = e1;
+      if (threadIdx.x == 0) {
+        const int* ex = A.xexcl + U.excl_base + b;
+        int e0 = ex[0], e1 = ex[1];
+        if (rec.w & kExpSplit) {  // a part of the bucket: narrow the slice
+          e0 = lower_bound_g(A.idx, e0, e1, max(clo, a + 1));
+          e1 = lower_bound_g(A.idx, e0, e1, chi);
+        }
+        s_e0 = e0;
+        s_e1 = e1;
+      }
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULLMASK, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (lane == 31) s_wsum[wid] = make_int2(incl, 0);
+      __syncthreads();
+      int before = 0, total = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const int v = s_wsum[w].x;
+        if (w < wid) before += v;
+        total += v;
+      }
+      if (tt < nt) s_pre[tt] = before + incl - len;
+      if (threadIdx.x == 0) s_pre[nt] = total;
     }
     __syncthreads();
+    if (threadIdx.x == 0) {  // look-ahead: claim and fetch the next item while this one runs
+      s_next = *(volatile u32*)&A.ctr->full ? ~0ull : atomicAdd(claim, 1ull);
+      fetch(s_next, s_rec_next, s_unit_next);
+    }
     auto insert = [&](int c, V wc) {
       if (dense) {
         const int p = swz(c - lg);
@@ -352,24 +394,43 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
         }
       }
     };
-    // insert the bucket's records, warps taking the tiles round-robin
-    for (int tt = wid; tt < U.T; tt += NW) {  // warp-uniform trips
-      const int p0 = s_p0[tt], p1 = s_p1[tt];
-      const u64 rb = s_rb[tt];
-      for (int i = p0 + lane; i < p1; i += 32) {
-        int c;
-        V w;
-        if (V64) {
-          const int2 r = reinterpret_cast<const int2*>(A.xrec)[rb + i];
-          c = r.x;
-          w = (V)__ldg(A.wt + r.y);
-        } else {
-          c = reinterpret_cast<const int*>(A.xrec)[rb + i];
-          w = (V)1;
+    // insert the bucket's records: warp w takes the flattened records
+    // [w R / NW, (w + 1) R / NW), 32 consecutive ones per step
+    {
+      const int R = s_pre[nt];
+      const int r0 = (int)(((long long)R * wid) / NW), r1 = (int)(((long long)R * (wid + 1)) / NW);
+      int tt = 0;
+      {  // the run holding r0 (last tt with s_pre[tt] <= r0)
+        int l = 0, h = nt;
+        while (h - l > 1) {
+          const int m = (l + h) >> 1;
+          if (s_pre[m] <= r0) l = m; else h = m;
         }
-        if (c >= clo && c < chi) insert(c, w);
+        tt = l;
       }
-      if (!dense && *(volatile int*)&s_overflow) break;
+      for (int rb0 = r0; rb0 < r1; rb0 += 32) {  // warp-uniform trips
+        const int r = rb0 + lane;
+        if (r < r1) {
+          int t = tt;
+          while (s_pre[t + 1] <= r) ++t;
+          const u64 at = s_rb[t] + (u64)(s_p0[t] + (r - s_pre[t]));
+          int c;
+          V w;
+          if (V64) {
+            const int2 x = reinterpret_cast<const int2*>(A.xrec)[at];
+            c = x.x;
+            w = (V)__ldg(A.wt + x.y);
+          } else {
+            c = reinterpret_cast<const int*>(A.xrec)[at];
+            w = (V)1;
+          }
+          if (c >= clo && c < chi) insert(c, w);
+        }
+        // the run of the warp's next first record
+        const int rn = min(rb0 + 32, r1 - 1);
+        while (tt + 1 < nt && s_pre[tt + 1] <= rn) ++tt;
+        if (!dense && *(volatile int*)&s_overflow) break;
+      }
     }
     __syncthreads();
     if (!dense && s_overflow) {
@@ -454,7 +515,6 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
       if (f < A.failed_cap) A.failed[f] = rec;
       else A.ctr->error = 1u;
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) n_cand += __shfl_xor_sync(FULLMASK, n_cand, o);
@@ -584,11 +644,12 @@ lp_status exp_setup(Graph& g, ScanArgs& A, u64 nexp, long long batch_wedges, boo
     // tiles of at least 4K wedges, at most kExpMaxTiles per unit (the count
     // pass loads a bucket's runs of every tile at once)
     U.tile_w = (int)std::max<long long>(4096, (U.W + kExpMaxTiles - 1) / kExpMaxTiles);
+    U.tile_w = (U.tile_w + kSub - 1) / kSub * kSub;
     U.T = (int)((U.W + U.tile_w - 1) / U.tile_w);
     U.arc_base = arcs;
     arcs += (long long)U.kept + 1;
     U.tfirst_base = tfirsts;
-    tfirsts += (long long)U.T + 1;
+    tfirsts += (long long)U.T * kSub + 1;
     U.excl_base = excls;
     excls += (long long)U.nb + 1;
     wmax = std::max<u64>(wmax, (u64)U.W);
