@@ -127,6 +127,8 @@ typedef struct {
                               expand passes (timing on; also in tier_ms[3])   */
   int32_t exp_units;       /* sources of the expand-and-count tier            */
   int32_t exp_batches;     /* their expand batches                            */
+  int64_t exp_items;       /* count items (buckets) run, re-queued ones included */
+  int64_t exp_dense_units; /* units counted in dense windows (the rest: hash)   */
 } lp_stats;
 
 /*

@@ -47,7 +47,8 @@ class lp_stats(ctypes.Structure):
                 ("tier_arcs", ctypes.c_int64 * 4), ("tier_kept", ctypes.c_int64 * 4),
                 ("tier_launches", ctypes.c_int32 * 4), ("tier_ms", ctypes.c_float * 4),
                 ("phase_cycles", ctypes.c_int64 * 6), ("ms_expand", ctypes.c_float),
-                ("exp_units", ctypes.c_int32), ("exp_batches", ctypes.c_int32)]
+                ("exp_units", ctypes.c_int32), ("exp_batches", ctypes.c_int32),
+                ("exp_items", ctypes.c_int64), ("exp_dense_units", ctypes.c_int64)]
 
 
 class lp_serve_opts(ctypes.Structure):

@@ -826,6 +826,7 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
       CU(cudaMemcpy(splits.data(), g.s_split.p, sizeof(int4) * h.nsplit, cudaMemcpyDeviceToHost));
     const u64 done[4] = {std::min<u64>(h.claim_w, Q.n[0]), std::min<u64>(h.claim_m, Q.n[1]),
                          std::min<u64>(h.claim_c, large_n), std::min<u64>(h.claim_x, Q.n[3])};
+    t_stats.exp_items += (int64_t)done[3];
     const u64 valid = std::min<u64>(h.cand_cnt, C);
     t_stats.splits += (int32_t)h.nsplit;
     if (h.full || (seed && valid >= (u64)k)) {
@@ -896,6 +897,7 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
   t_stats.ms_expand = X.ms_expand;
   t_stats.exp_units = (int32_t)X.units.size();
   t_stats.exp_batches = (int32_t)X.batches.size();
+  for (const ExpUnit& U : X.units) t_stats.exp_dense_units += (U.flags & kExpDense) ? 1 : 0;
   tm.mark(2);
   // final selection: the best k, sorted
   u64 nsorted = kept;
