@@ -369,6 +369,10 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
       s_next = *(volatile u32*)&A.ctr->full ? ~0ull : atomicAdd(claim, 1ull);
       fetch(s_next, s_rec_next, s_unit_next);
     }
+    // a table that receives at most `limit` records cannot fill: then no
+    // distinct-key count and no overflow test is needed
+    const int R = s_pre[nt];
+    const bool guard = !dense && R > limit;
     auto insert = [&](int c, V wc) {
       if (dense) {
         const int p = swz(c - lg);
@@ -384,6 +388,8 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
           const u32 hc = h + ((old + l < old) ? 1u : 0u);
           if (hc) atomicAdd(dhi + p, hc);
         }
+      } else if (!guard) {
+        hash_add<V>(keys, vals, logcap, c, wc);
       } else {
         if (*(volatile int*)&s_overflow) return;
         const int rc = hash_add<V>(keys, vals, logcap, c, wc);
@@ -397,7 +403,6 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
     // insert the bucket's records: warp w takes the flattened records
     // [w R / NW, (w + 1) R / NW), 32 consecutive ones per step
     {
-      const int R = s_pre[nt];
       const int r0 = (int)(((long long)R * wid) / NW), r1 = (int)(((long long)R * (wid + 1)) / NW);
       int tt = 0;
       {  // the run holding r0 (last tt with s_pre[tt] <= r0)
@@ -429,11 +434,11 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
         // the run of the warp's next first record
         const int rn = min(rb0 + 32, r1 - 1);
         while (tt + 1 < nt && s_pre[tt + 1] <= rn) ++tt;
-        if (!dense && *(volatile int*)&s_overflow) break;
+        if (guard && *(volatile int*)&s_overflow) break;
       }
     }
     __syncthreads();
-    if (!dense && s_overflow) {
+    if (guard && s_overflow) {
       // hand the item back for splitting; leave the table empty
       for (int i = threadIdx.x * 4; i < nslots; i += kCountThreads * 4) {
         *reinterpret_cast<int4*>(keys + i) = make_int4(0, 0, 0, 0);

@@ -149,15 +149,6 @@ __global__ void k_pair_scatter(const lp_link* __restrict__ links, u64 n,
     perm[atomicAdd(&sc[pair_owner(links[i], off)].x, 1)] = (int)i;
 }
 
-// Position of the first entry >= key in the sorted idx[lo, hi).
-__device__ __forceinline__ int pair_lower_bound(const int* __restrict__ idx, int lo, int hi, int key) {
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(idx + mid) < key) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
 constexpr int kPairHashLog = 14;                    // hash-set slots (64 KB of keys)
 constexpr int kPairHashMaxDeg = 1 << (kPairHashLog - 1);
 
@@ -180,7 +171,8 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
                                                             const int* __restrict__ idx,
                                                             const Arc* __restrict__ arc, int cap,
                                                             int nwords, int n,
-                                                            u32* __restrict__ claim) {
+                                                            u32* __restrict__ claim,
+                                                            int* __restrict__ cur) {
   extern __shared__ u32 bits[];
   __shared__ u32 s_g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -241,20 +233,37 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
         const int v = L.u == u ? L.v : L.u;
         int c = 0;
         const int vs = off[v], ve = off[v + 1];
-        const int ee = one_window ? ve : pair_lower_bound(idx, vs, ve, w1);
-        int e = (one_window ? vs : pair_lower_bound(idx, vs, ve, w0)) + lane;
-        for (; e + 96 < ee; e += 128) {  // four loads in flight per lane
-          const int b0 = __ldg(idx + e) - w0, b1 = __ldg(idx + e + 32) - w0,
-                    b2 = __ldg(idx + e + 64) - w0, b3 = __ldg(idx + e + 96) - w0;
-          c += ((bits[b0 >> 5] >> (b0 & 31)) & 1u) + ((bits[b1 >> 5] >> (b1 & 31)) & 1u) +
-               ((bits[b2 >> 5] >> (b2 & 31)) & 1u) + ((bits[b3 >> 5] >> (b3 & 31)) & 1u);
-        }
-        for (; e < ee; e += 32) {
-          const int b = __ldg(idx + e) - w0;
-          c += (bits[b >> 5] >> (b & 31)) & 1u;
+        // Gamma_v is sorted and the windows ascend: this window's entries
+        // start where the previous window's ended (a cursor per link), and
+        // end at the first entry >= w1, found by the walk itself
+        int e0 = w0 == 0 ? vs : cur[G.y + j];
+        int next = ve;
+        for (;;) {  // warp-uniform trips; four loads in flight per lane
+          int bb[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int e = e0 + 32 * k + lane;
+            bb[k] = e < ve ? __ldg(idx + e) : INT_MAX;
+          }
+          bool stop = false;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const bool in = bb[k] < w1;
+            const int b = bb[k] - w0;
+            c += in ? ((bits[b >> 5] >> (b & 31)) & 1u) : 0u;
+            const u32 m = __ballot_sync(FULLMASK, !in);
+            if (m) {  // warp-uniform
+              next = e0 + 32 * k + __ffs(m) - 1;
+              stop = true;
+              break;
+            }
+          }
+          if (stop) break;
+          e0 += 128;
         }
         c = __reduce_add_sync(FULLMASK, (u32)c);
         if (lane == 0) {
+          if (!one_window) cur[G.y + j] = min(next, ve);
           if (w0 == 0) links[li].cn = c;
           else links[li].cn += c;
         }
@@ -270,15 +279,16 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
 }
 
 // Scratch layout: sc int2[n + 1], cnt int[n + 1], perm int[links], groups
-// int4[n], sums int2[chunks], claim u32; every part 256-byte aligned (groups
-// are written as int4).
+// int4[n], sums int2[chunks], claim u32, window cursors int[links]; every
+// part 256-byte aligned (groups are written as int4).
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t pair_groups_scratch(int n, u64 nlinks) {
   const size_t n1 = (size_t)n + 1;
   return align256(n1 * sizeof(int2)) + align256(n1 * sizeof(int)) + align256(nlinks * sizeof(int)) +
          align256((size_t)n * sizeof(int4)) +
-         align256(((n1 + kScanChunk - 1) / kScanChunk) * sizeof(int2)) + 256;
+         align256(((n1 + kScanChunk - 1) / kScanChunk) * sizeof(int2)) + 256 +
+         align256(nlinks * sizeof(int));
 }
 
 // Counts of links[0, n), grouped by the endpoint of larger degree; scratch of pair_groups_scratch bytes.
@@ -300,6 +310,8 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
   int2* sums = reinterpret_cast<int2*>(p);
   p += align256((size_t)nb * sizeof(int2));
   u32* claim = reinterpret_cast<u32*>(p);
+  p += 256;
+  int* cur = reinterpret_cast<int*>(p);
   cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)n1 * sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(claim, 0, sizeof(u32), st);
   if (e != cudaSuccess) return e;
@@ -321,7 +333,7 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   k_pair_cn_groups<<<nsm, 1024, smem, st>>>(links, perm, groups, sc + nv, off, idx, arc, cap,
-                                            nwords, nv, claim);
+                                            nwords, nv, claim, cur);
   if (launches) *launches += 7;
   return cudaGetLastError();
 }
