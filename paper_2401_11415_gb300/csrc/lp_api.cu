@@ -599,11 +599,12 @@ static cudaError_t build_queue(Graph& g, Graph::Scratch& dst, const std::vector<
   return e;
 }
 
-// Rebuild the three queues: re-queued records first, then the unclaimed
+// Rebuild the four queues: re-queued records first, then the unclaimed
 // remainder of each queue.
 static cudaError_t rebuild_queues(Graph& g, Queues& Q, const std::vector<int4>* heads,
                                   const u64* done) {
   for (int t = 0; t < 4; ++t) {
+    if (Q.n[t] == 0 && heads[t].empty()) continue;  // stays empty
     u64 n2 = 0;
     cudaError_t e = build_queue(g, *Q.alt[t], heads[t], sp<int4>(*Q.cur[t]), done[t], Q.n[t], &n2);
     if (e != cudaSuccess) return e;
@@ -1060,11 +1061,13 @@ static lp_status predict_sources(Graph& g, int measure, int cap, const int* d_sr
   u64 partial_cap = h.nitem + 16;
   CU(ensure(g, g.s_partial, sizeof(TopEnt) * partial_cap * k));
   CU(ensure(g, g.s_phdr, sizeof(int2) * partial_cap));
-  Queues Q = {{&g.s_warpq, &g.s_medq, &g.s_itemq}, {&g.s_warpq2, &g.s_medq2, &g.s_itemq2},
-              {h.nwarp, h.nmed, h.nitem}};
+  // (the expand-and-count tier is global-mode only: its queue stays empty)
+  Queues Q = {{&g.s_warpq, &g.s_medq, &g.s_itemq, &g.s_countq},
+              {&g.s_warpq2, &g.s_medq2, &g.s_itemq2, &g.s_countq2},
+              {h.nwarp, h.nmed, h.nitem, 0}};
   u64 npartial = 0;
   std::vector<int4> splits;
-  std::vector<int4> heads[3];
+  std::vector<int4> heads[4];
   for (int round = 0; Q.n[0] + Q.n[1] + Q.n[2] > 0; ++round) {
     if (round > 10000) return fail(LP_EINTERNAL, "lp_predict_sources: no progress");
     Counters z{};
@@ -1092,7 +1095,7 @@ static lp_status predict_sources(Graph& g, int measure, int cap, const int* d_sr
     for (auto& hd : heads) hd.clear();
     for (const int4& r : splits) split_item(r, A.big_span, heads[2]);
     for (int4& r : heads[2]) r.w &= ~kItemSingle;
-    const u64 done[3] = {Q.n[0], Q.n[1], Q.n[2]};  // no buffer: everything claimed ran
+    const u64 done[4] = {Q.n[0], Q.n[1], Q.n[2], 0};  // no buffer: everything claimed ran
     CU(rebuild_queues(g, Q, heads, done));
     if (npartial + Q.n[2] + 16 > partial_cap) {
       // grow the partial store, keeping what is there
