@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
       }
     };
     // insert the bucket's records: warp w takes the flattened records
-    // [w R / NW, (w + 1) R / NW), 32 consecutive ones per step
+    // [w R / NW, (w + 1) R / NW)
     {
       const int r0 = (int)(((long long)R * wid) / NW), r1 = (int)(((long long)R * (wid + 1)) / NW);
       int tt = 0;
@@ -413,26 +413,36 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
         }
         tt = l;
       }
-      for (int rb0 = r0; rb0 < r1; rb0 += 32) {  // warp-uniform trips
-        const int r = rb0 + lane;
-        if (r < r1) {
-          int t = tt;
-          while (s_pre[t + 1] <= r) ++t;
-          const u64 at = s_rb[t] + (u64)(s_p0[t] + (r - s_pre[t]));
-          int c;
-          V w;
-          if (V64) {
-            const int2 x = reinterpret_cast<const int2*>(A.xrec)[at];
-            c = x.x;
-            w = (V)__ldg(A.wt + x.y);
-          } else {
-            c = reinterpret_cast<const int*>(A.xrec)[at];
-            w = (V)1;
+      // 128 records per step, four loads in flight per lane before any insert
+      for (int rb0 = r0; rb0 < r1; rb0 += 128) {  // warp-uniform trips
+        int cc[4];
+        V ww[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int r = rb0 + 32 * k + lane;
+          cc[k] = -1;
+          ww[k] = 0;
+          if (r < r1) {
+            int t = tt;
+            while (s_pre[t + 1] <= r) ++t;
+            const u64 at = s_rb[t] + (u64)(s_p0[t] + (r - s_pre[t]));
+            if (V64) {
+              const int2 x = reinterpret_cast<const int2*>(A.xrec)[at];
+              cc[k] = x.x;
+              ww[k] = (V)x.y;  // |Gamma_b| until the weight lookup below
+            } else {
+              cc[k] = reinterpret_cast<const int*>(A.xrec)[at];
+              ww[k] = (V)1;
+            }
           }
-          if (c >= clo && c < chi) insert(c, w);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = cc[k];
+          if (c >= clo && c < chi) insert(c, V64 ? (V)__ldg(A.wt + (int)ww[k]) : (V)1);
         }
         // the run of the warp's next first record
-        const int rn = min(rb0 + 32, r1 - 1);
+        const int rn = min(rb0 + 128, r1 - 1);
         while (tt + 1 < nt && s_pre[tt + 1] <= rn) ++tt;
         if (guard && *(volatile int*)&s_overflow) break;
       }

@@ -236,6 +236,22 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
         // Gamma_v is sorted and the windows ascend: this window's entries
         // start where the previous window's ended (a cursor per link), and
         // end at the first entry >= w1, found by the walk itself
+        if (one_window) {  // every id in the bitmap: the whole list, no bound
+          int e = vs + lane;
+          for (; e + 96 < ve; e += 128) {  // four loads in flight per lane
+            const int b0 = __ldg(idx + e), b1 = __ldg(idx + e + 32), b2 = __ldg(idx + e + 64),
+                      b3 = __ldg(idx + e + 96);
+            c += ((bits[b0 >> 5] >> (b0 & 31)) & 1u) + ((bits[b1 >> 5] >> (b1 & 31)) & 1u) +
+                 ((bits[b2 >> 5] >> (b2 & 31)) & 1u) + ((bits[b3 >> 5] >> (b3 & 31)) & 1u);
+          }
+          for (; e < ve; e += 32) {
+            const int b = __ldg(idx + e);
+            c += (bits[b >> 5] >> (b & 31)) & 1u;
+          }
+          c = __reduce_add_sync(FULLMASK, (u32)c);
+          if (lane == 0) links[li].cn = c;
+          continue;
+        }
         int e0 = w0 == 0 ? vs : cur[G.y + j];
         int next = ve;
         for (;;) {  // warp-uniform trips; four loads in flight per lane
@@ -263,7 +279,7 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
         }
         c = __reduce_add_sync(FULLMASK, (u32)c);
         if (lane == 0) {
-          if (!one_window) cur[G.y + j] = min(next, ve);
+          cur[G.y + j] = min(next, ve);
           if (w0 == 0) links[li].cn = c;
           else links[li].cn += c;
         }
