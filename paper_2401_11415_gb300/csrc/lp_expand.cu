@@ -400,10 +400,12 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
         }
       }
     };
-    // insert the bucket's records: warp w takes the flattened records
-    // [w R / NW, (w + 1) R / NW)
-    {
-      const int r0 = (int)(((long long)R * wid) / NW), r1 = (int)(((long long)R * (wid + 1)) / NW);
+    // insert the bucket's records: warp w > 0 takes the flattened records
+    // [(w - 1) R / (NW - 1), w R / (NW - 1)); warp 0 fetches the next item
+    // meanwhile (its chain of dependent loads stays off the barrier's path)
+    if (wid > 0) {
+      const int r0 = (int)(((long long)R * (wid - 1)) / (NW - 1));
+      const int r1 = (int)(((long long)R * wid) / (NW - 1));
       int tt = 0;
       {  // the run holding r0 (last tt with s_pre[tt] <= r0)
         int l = 0, h = nt;
