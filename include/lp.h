@@ -344,7 +344,11 @@ typedef struct {
   int32_t max_k;             /* largest k accepted, <= LP_MAX_TOPK_PER_SOURCE (0: 16) */
   int32_t paused;            /* 1: queue requests but start no batch until
                                 lp_serve_resume                                   */
-  int32_t reserved[3];
+  int32_t mode;              /* 0: a resident kernel serves the requests (below);
+                                1: host worker threads run batches               */
+  int32_t idle_polls;        /* mode 0: polls (about 4 us apart) a resident CTA
+                                waits for work before it leaves (0: 2500)        */
+  int32_t reserved;
 } lp_serve_opts;
 
 typedef struct {
@@ -352,7 +356,11 @@ typedef struct {
   int64_t completed;         /* requests finished (result ready or failed)        */
   int64_t batches;           /* device batches run                                */
   int64_t batched_sources;   /* sources over all batches                          */
-  int64_t max_batch_requests;/* most requests merged into one batch               */
+  int64_t max_batch_requests;/* most requests merged into one batch (mode 0: most
+                                requests in flight on the device at once)        */
+  int64_t kernel_launches;   /* mode 0: launches of the resident kernel (it leaves
+                                after idle_polls polls without work and is
+                                launched again when work arrives)                */
 } lp_serve_stats;
 
 /* Start a server on graph g (which must outlive it).  opts may be NULL.

@@ -278,6 +278,39 @@ cudaError_t launch_exp_tiles(const ScanArgs& A, const ExpUnit* units, const int*
                              const int* tfirst, void* rec, u64* tile_rec, int* pre,
                              cudaStream_t st);
 cudaError_t launch_exp_count(const ScanArgs& A, const int4* q, u64 nq, cudaStream_t st);
+// Resident serving kernel (lp_serve_dev.cu).  A request slot's parameters,
+// written by the host before its work items are published.
+struct SrvReq {
+  int measure, cap, k, n_src;
+  long long src_off;  // first source in the source pool
+  long long out_off;  // first link of row 0 in the output pool (rows of k links)
+  long long target;   // value of finished[slot] once the request is complete
+  unsigned seq;       // written to done[slot] on completion
+  int pad;
+};
+struct SrvArgs {
+  const int* off;
+  const int* idx;
+  const int* deg;
+  const Arc* arc;
+  const u64* wt;                      // AA then RA weights by degree
+  int n, dmax, fixbits, idle_polls;
+  const int2* ring;                   // work items {slot, source index} (host memory)
+  unsigned long long ring_cap;
+  const unsigned long long* tail;     // items published (host memory)
+  unsigned long long* head;           // items claimed (device)
+  const SrvReq* reqs;                 // request slots (host memory)
+  const int* src_pool;                // sources (host memory)
+  lp_link* out_pool;                  // result rows (host memory)
+  unsigned long long* finished;       // sources finished per slot (device)
+  unsigned* done;                     // completion word per slot (host memory)
+  unsigned* status;                   // device error word (host memory)
+  const unsigned* stop;               // 1: leave at once when idle (host memory)
+};
+size_t serve_smem_bytes(int max_k);
+cudaError_t launch_serve(const SrvArgs& S, int max_k, cudaStream_t st);
+cudaError_t preload_serve_kernel();
+
 // Host plan of the expand-and-count tier for one global call: the units in
 // batches of at most expand_batch wedges (a larger unit alone).
 struct ExpBatch {

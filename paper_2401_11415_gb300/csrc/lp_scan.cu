@@ -1231,94 +1231,6 @@ __global__ void k_emit_sources(const TopEnt* __restrict__ top, const int* __rest
   out[i] = make_link(measure, sources[r], x.c, x.num, x.den, (u64)x.cn, fixbits);
 }
 
-// Sum over the common neighbours b of (u, v) with |Gamma_b| <= cap of 1
-// (wt null: the count) or of wt[|Gamma_b|] (the AA / RA fixed-point weight,
-// so the sum is the key the scan accumulated: integer addition does not
-// depend on the order).  One warp per pair; every lane returns the total.
-// x is the endpoint of smaller degree.  Short Gamma_x (or a much longer
-// Gamma_y): each lane takes elements b of Gamma_x (hub test from the arc
-// table) and looks the other endpoint up in the shorter of Gamma_b and
-// Gamma_y.  Two long lists of similar length: a merge-path intersection
-// across the lanes.
-__device__ __forceinline__ u64 pair_common(int u, int v, const int* __restrict__ off,
-                                           const int* __restrict__ idx,
-                                           const int* __restrict__ deg,
-                                           const Arc* __restrict__ arc, int cap,
-                                           const u64* __restrict__ wt) {
-  const int lane = lane_id();
-  int x = u, y = v;
-  if (off[x + 1] - off[x] > off[y + 1] - off[y]) {
-    const int t = x;
-    x = y;
-    y = t;
-  }
-  const int xs = off[x], xe = off[x + 1];
-  const int ys = off[y], ye = off[y + 1];
-  const int dy = ye - ys;
-  const int dx = xe - xs;
-  u64 c = 0;
-  if (dx <= 64 || dy > 16 * dx || cap < 256) {
-    // short Gamma_x, a much longer Gamma_y or a low hub limit (most b are
-    // skipped without a search): look each b of Gamma_x up
-    for (int e = xs + lane; e < xe; e += 32) {
-      const Arc t = arc[e];  // b = t.w, |Gamma_b| = t.z, Gamma_b ends at t.y
-      const int b = t.w, db = t.z;
-      if (db > cap) continue;
-      bool hit;
-      if (db <= dy) {
-        const int be = t.y, bs = be - db;
-        const int p = lower_bound_interp(idx, bs, be, y);
-        hit = p < be && __ldg(idx + p) == y;
-      } else {
-        const int p = lower_bound_interp(idx, ys, ye, b);
-        hit = p < ye && __ldg(idx + p) == b;
-      }
-      if (hit) c += wt ? __ldg(wt + db) : 1ull;
-    }
-  } else {
-    // comparable long lists: both walked in 32-element tiles, one element
-    // per lane.  Each lane looks its Gamma_x element up in the current Gamma_y
-    // tile (binary search over the lanes); then the tile with the smaller last
-    // element moves on (both on a tie), with the next tiles already loading.
-    // A common element is in both tiles during exactly one step.
-    const int* X = idx + xs;
-    const int* Y = idx + ys;
-    int i = 0, j = 0;
-    int xv = lane < dx ? __ldg(X + lane) : INT_MAX;
-    int yv = lane < dy ? __ldg(Y + lane) : INT_MAX;
-    int xn = 32 + lane < dx ? __ldg(X + 32 + lane) : INT_MAX;
-    int yn = 32 + lane < dy ? __ldg(Y + 32 + lane) : INT_MAX;
-    while (i < dx && j < dy) {  // warp-uniform
-      int p = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1)
-        if (__shfl_sync(FULLMASK, yv, p + step - 1) < xv) p += step;
-      const int yp = __shfl_sync(FULLMASK, yv, p);  // every lane takes part
-      bool hit = xv != INT_MAX && yp == xv;
-      int db = 0;
-      if (hit && (cap < INT_MAX || wt)) {
-        db = __ldg(deg + xv);
-        hit = db <= cap;
-      }
-      if (hit) c += wt ? __ldg(wt + db) : 1ull;
-      const int lx = __shfl_sync(FULLMASK, xv, 31), ly = __shfl_sync(FULLMASK, yv, 31);
-      if (lx <= ly) {
-        i += 32;
-        xv = xn;
-        xn = i + 32 + lane < dx ? __ldg(X + i + 32 + lane) : INT_MAX;
-      }
-      if (ly <= lx) {
-        j += 32;
-        yv = yn;
-        yn = j + 32 + lane < dy ? __ldg(Y + j + 32 + lane) : INT_MAX;
-      }
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULLMASK, c, o);
-  return c;
-}
-
 // Common neighbours of AA / RA links (whose tables hold weight sums rather
 // than counts), one warp per link.
 __global__ void k_pair_cn(lp_link* __restrict__ links, const int* __restrict__ cnt_rows, int k,

@@ -1,7 +1,21 @@
 // lp_serve.cu -- continuous batching of per-source queries (lp_serve_*).
 //
-// Requests (per-source top-k queries of uneven size) are queued from any
-// thread.  Each of `slots` workers owns a shadow view of the graph (shared
+// Mode 0 (the default): a resident kernel (lp_serve_dev.cu) serves the
+// requests.  An admitted request gets a request slot and room in two pools
+// of pinned host memory the GPU reads and writes directly: its sources and
+// its result rows.  The host writes them, one work item per source into a
+// ring, and then advances the ring's published count; the kernel's CTAs claim
+// the items and raise the slot's completion word after the last source.
+// Admission is by that memory: a request waits on the host until its sources
+// and rows (4 + 16 k bytes per source) fit in the pools, a slot is free and
+// the ring has room.  Finished requests are collected by any call that polls
+// (submit, wait, poll): their rows are copied out and their memory freed, so
+// waiting requests are admitted as memory frees up.  The kernel leaves when
+// it finds no work for idle_polls polls; a call that sees published work and
+// no kernel running launches it again.
+//
+// Mode 1: requests (per-source top-k queries of uneven size) are queued from
+// any thread.  Each of `slots` workers owns a shadow view of the graph (shared
 // device arrays, its own stream and scratch) plus device and pinned host
 // buffers sized for max_batch_sources sources.  A worker takes the oldest
 // pending request and every other pending request with the same (measure,
@@ -12,7 +26,9 @@
 // its own source (the per-source scan has no cross-source state), so a result
 // is identical alone and in any mix.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <map>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -34,6 +50,73 @@ struct Request {
   lp_status status = LP_OK;
   std::string error;  // the worker's error text when status != LP_OK
   bool done = false;
+  // mode 0: where the admitted request lives
+  bool admitted = false;
+  int slot = -1;
+  long long off = 0;  // first source in the pools
+  unsigned seq = 0;
+};
+
+// First-fit allocator of [0, cap) ranges (pool entries).
+struct RangeAlloc {
+  std::map<long long, long long> free_;  // start -> length
+  void init(long long cap) {
+    free_.clear();
+    free_[0] = cap;
+  }
+  long long take(long long n) {
+    for (auto it = free_.begin(); it != free_.end(); ++it)
+      if (it->second >= n) {
+        const long long at = it->first, len = it->second;
+        free_.erase(it);
+        if (len > n) free_[at + n] = len - n;
+        return at;
+      }
+    return -1;
+  }
+  void give(long long at, long long n) {
+    auto nx = free_.lower_bound(at);
+    if (nx != free_.end() && at + n == nx->first) {
+      n += nx->second;
+      nx = free_.erase(nx);
+    }
+    if (nx != free_.begin()) {
+      auto pv = std::prev(nx);
+      if (pv->first + pv->second == at) {
+        pv->second += n;
+        return;
+      }
+    }
+    free_[at] = n;
+  }
+};
+
+// Mode 0 state: pools and ring in pinned host memory the GPU maps, claim and
+// finish counters on the device.
+struct DevLoop {
+  cudaStream_t stream = nullptr;  // the resident kernel's stream
+  lp::SrvArgs args{};
+  int2* ring = nullptr;
+  unsigned long long* tail = nullptr;
+  lp::SrvReq* reqs = nullptr;
+  int* src_pool = nullptr;
+  lp_link* out_pool = nullptr;
+  unsigned* done = nullptr;
+  unsigned* status = nullptr;
+  unsigned* stop = nullptr;
+  unsigned long long* d_head = nullptr;
+  unsigned long long* d_finished = nullptr;
+  long long pool_cap = 0;        // sources the pools hold
+  long long ring_cap = 0;
+  int nslots = 0;                // request slots
+  unsigned long long published = 0, retired = 0;  // work items
+  std::vector<long long> slot_total;  // sources ever assigned to each slot
+  std::vector<int> free_slots;
+  RangeAlloc pool;
+  std::deque<Request*> waiting;  // submitted, not admitted yet
+  std::vector<Request*> inflight;
+  bool running = false;
+  unsigned next_seq = 1;
 };
 
 struct Slot {
@@ -52,6 +135,7 @@ struct lp_server {
   const lp_graph* g = nullptr;
   lp::Graph* base = nullptr;
   lp_serve_opts opts{};
+  DevLoop dev;
   std::vector<Slot> slots;
   std::vector<std::thread> workers;
   std::mutex mu;
@@ -150,6 +234,204 @@ void worker_main(lp_server* S, int si) {
 
 lp_status serve_fail(lp_status s, const char* msg) { return lp::report_error(s, msg); }
 
+// ------------------------------------------------------------ mode 0 ----
+
+void dev_free(DevLoop& D) {
+  if (D.stream) {
+    cudaStreamSynchronize(D.stream);
+    cudaStreamDestroy(D.stream);
+  }
+  cudaFreeHost(D.ring);
+  cudaFreeHost(D.tail);
+  cudaFreeHost(D.reqs);
+  cudaFreeHost(D.src_pool);
+  cudaFreeHost(D.out_pool);
+  cudaFreeHost(D.done);
+  cudaFreeHost(D.status);
+  cudaFreeHost(D.stop);
+  cudaFree(D.d_head);
+  cudaFree(D.d_finished);
+  D = DevLoop();
+}
+
+template <typename T>
+cudaError_t mapped(T** host, size_t count, T** dev) {
+  cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(host), sizeof(T) * (count ? count : 1),
+                                cudaHostAllocMapped);
+  if (e != cudaSuccess) return e;
+  std::memset(*host, 0, sizeof(T) * (count ? count : 1));
+  return cudaHostGetDevicePointer(reinterpret_cast<void**>(dev), *host, 0);
+}
+
+cudaError_t dev_open(lp_server* S) {
+  DevLoop& D = S->dev;
+  const lp::Graph& g = *S->base;
+  D.pool_cap = (long long)S->opts.max_batch_sources * S->opts.slots;
+  D.ring_cap = D.pool_cap;
+  D.nslots = std::min(S->opts.max_pending, 65536);
+  lp::SrvArgs& A = D.args;
+  int2* ring_d = nullptr;
+  unsigned long long* tail_d = nullptr;
+  lp::SrvReq* reqs_d = nullptr;
+  int* src_d = nullptr;
+  lp_link* out_d = nullptr;
+  unsigned *done_d = nullptr, *status_d = nullptr, *stop_d = nullptr;
+  cudaError_t e = mapped(&D.ring, (size_t)D.ring_cap, &ring_d);
+  if (e == cudaSuccess) e = mapped(&D.tail, 1, &tail_d);
+  if (e == cudaSuccess) e = mapped(&D.reqs, (size_t)D.nslots, &reqs_d);
+  if (e == cudaSuccess) e = mapped(&D.src_pool, (size_t)D.pool_cap, &src_d);
+  if (e == cudaSuccess) e = mapped(&D.out_pool, (size_t)D.pool_cap * S->opts.max_k, &out_d);
+  if (e == cudaSuccess) e = mapped(&D.done, (size_t)D.nslots, &done_d);
+  if (e == cudaSuccess) e = mapped(&D.status, 1, &status_d);
+  if (e == cudaSuccess) e = mapped(&D.stop, 1, &stop_d);
+  if (e == cudaSuccess) e = cudaMalloc(&D.d_head, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&D.d_finished, sizeof(unsigned long long) * D.nslots);
+  if (e == cudaSuccess) e = cudaMemset(D.d_head, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(D.d_finished, 0, sizeof(unsigned long long) * D.nslots);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&D.stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return e;
+  A.off = g.d_off;
+  A.idx = g.d_idx;
+  A.deg = g.d_deg;
+  A.arc = g.d_arc;
+  A.wt = g.d_wt;
+  A.n = g.n;
+  A.dmax = g.dmax;
+  A.fixbits = g.fixbits;
+  A.idle_polls = S->opts.idle_polls;
+  A.ring = ring_d;
+  A.ring_cap = (unsigned long long)D.ring_cap;
+  A.tail = tail_d;
+  A.head = D.d_head;
+  A.reqs = reqs_d;
+  A.src_pool = src_d;
+  A.out_pool = out_d;
+  A.finished = D.d_finished;
+  A.done = done_d;
+  A.status = status_d;
+  A.stop = stop_d;
+  D.slot_total.assign(D.nslots, 0);
+  D.free_slots.clear();
+  for (int i = D.nslots - 1; i >= 0; --i) D.free_slots.push_back(i);
+  D.pool.init(D.pool_cap);
+  return cudaSuccess;
+}
+
+// S->mu held in every helper below.
+
+// Launch the resident kernel if work is outstanding and it is not running.
+void dev_ensure_running(lp_server* S) {
+  DevLoop& D = S->dev;
+  if (D.published == D.retired) return;
+  if (D.running) {
+    const cudaError_t q = cudaStreamQuery(D.stream);
+    if (q == cudaErrorNotReady) return;
+    D.running = false;
+    if (q != cudaSuccess) {
+      cudaGetLastError();
+      __atomic_store_n(D.status, 2u, __ATOMIC_RELEASE);  // the kernel failed
+      return;
+    }
+  }
+  if (__atomic_load_n(D.status, __ATOMIC_ACQUIRE) != 0) return;
+  if (lp::launch_serve(D.args, S->opts.max_k, D.stream) == cudaSuccess) {
+    D.running = true;
+    S->stats.kernel_launches += 1;
+  } else {
+    cudaGetLastError();
+    __atomic_store_n(D.status, 2u, __ATOMIC_RELEASE);
+  }
+}
+
+// Admit r if a slot, its pool room and ring room are free: write its
+// parameters, sources and work items, then publish.
+bool dev_admit(lp_server* S, Request* r) {
+  DevLoop& D = S->dev;
+  const long long n = (long long)r->sources.size();
+  if (D.free_slots.empty()) return false;
+  if ((long long)(D.published - D.retired) + n > D.ring_cap) return false;
+  const long long off = D.pool.take(n);
+  if (off < 0) return false;
+  const int slot = D.free_slots.back();
+  D.free_slots.pop_back();
+  r->slot = slot;
+  r->off = off;
+  r->seq = D.next_seq++;
+  if (D.next_seq == 0) D.next_seq = 1;
+  std::memcpy(D.src_pool + off, r->sources.data(), sizeof(int32_t) * n);
+  D.slot_total[slot] += n;
+  lp::SrvReq q;
+  q.measure = r->measure;
+  q.cap = r->cap;
+  q.k = r->k;
+  q.n_src = (int)n;
+  q.src_off = off;
+  q.out_off = off * S->opts.max_k;
+  q.target = D.slot_total[slot];
+  q.seq = r->seq;
+  q.pad = 0;
+  D.reqs[slot] = q;
+  for (long long i = 0; i < n; ++i)
+    D.ring[(D.published + (unsigned long long)i) % (unsigned long long)D.ring_cap] =
+        make_int2(slot, (int)i);
+  D.published += (unsigned long long)n;
+  __atomic_store_n(D.tail, D.published, __ATOMIC_RELEASE);  // everything above first
+  r->admitted = true;
+  D.inflight.push_back(r);
+  S->stats.batches += 1;
+  S->stats.batched_sources += n;
+  S->stats.max_batch_requests =
+      std::max<int64_t>(S->stats.max_batch_requests, (int64_t)D.inflight.size());
+  return true;
+}
+
+// Collect finished requests (copy their rows out, free their memory), then
+// admit waiting requests in arrival order while they fit.
+void dev_harvest(lp_server* S) {
+  DevLoop& D = S->dev;
+  const unsigned st = __atomic_load_n(D.status, __ATOMIC_ACQUIRE);
+  bool any = false;
+  for (size_t i = 0; i < D.inflight.size();) {
+    Request* r = D.inflight[i];
+    const bool fin = __atomic_load_n(D.done + r->slot, __ATOMIC_ACQUIRE) == r->seq;
+    if (!fin && st == 0) {
+      ++i;
+      continue;
+    }
+    const size_t n = r->sources.size(), k = (size_t)r->k;
+    if (fin && st == 0) {
+      r->out.resize(n * k);
+      r->counts.resize(n);
+      const lp_link* base = D.out_pool + (size_t)r->off * S->opts.max_k;
+      for (size_t j = 0; j < n; ++j) {
+        std::memcpy(r->out.data() + j * k, base + j * k, sizeof(lp_link) * k);
+        int c = 0;
+        while (c < (int)k && r->out[j * k + c].v >= 0) ++c;
+        r->counts[j] = c;
+      }
+      r->status = LP_OK;
+    } else {
+      r->status = st == 2 ? LP_ECUDA : LP_EINTERNAL;
+      r->error = st == 2 ? "the resident serving kernel failed" : "serving: device check failed";
+    }
+    r->done = true;
+    if (fin) {  // the slot and the pool room are free again
+      D.pool.give(r->off, (long long)n);
+      D.free_slots.push_back(r->slot);
+      D.retired += (unsigned long long)n;
+    }
+    D.inflight[i] = D.inflight.back();
+    D.inflight.pop_back();
+    S->stats.completed += 1;
+    any = true;
+  }
+  while (!S->paused && st == 0 && !D.waiting.empty() && dev_admit(S, D.waiting.front()))
+    D.waiting.pop_front();
+  dev_ensure_running(S);
+  if (any) S->cv_done.notify_all();
+}
+
 }  // namespace
 
 extern "C" {
@@ -163,8 +445,9 @@ lp_status lp_serve_open(const lp_graph* g, const lp_serve_opts* opts, lp_server*
   if (o.max_batch_sources == 0) o.max_batch_sources = 65536;
   if (o.max_pending == 0) o.max_pending = 65536;
   if (o.max_k == 0) o.max_k = 16;
+  if (o.idle_polls == 0) o.idle_polls = 2500;
   if (o.slots < 1 || o.slots > 8 || o.max_batch_sources < 1 || o.max_pending < 1 || o.max_k < 1 ||
-      o.max_k > LP_MAX_TOPK_PER_SOURCE)
+      o.max_k > LP_MAX_TOPK_PER_SOURCE || o.mode < 0 || o.mode > 1 || o.idle_polls < 1)
     return serve_fail(LP_EINVAL, "lp_serve_open: option out of range");
   lp_server* S = new (std::nothrow) lp_server();
   if (!S) return serve_fail(LP_ENOMEM, "lp_serve_open: host allocation");
@@ -172,6 +455,17 @@ lp_status lp_serve_open(const lp_graph* g, const lp_serve_opts* opts, lp_server*
   S->base = &lp::graph_of(g);
   S->opts = o;
   S->paused = o.paused != 0;
+  if (o.mode == 0) {
+    cudaError_t e = cudaSetDevice(S->base->device);
+    if (e == cudaSuccess) e = dev_open(S);
+    if (e != cudaSuccess) {
+      dev_free(S->dev);
+      delete S;
+      return lp::report_cuda(e, "lp_serve_open");
+    }
+    *out = S;
+    return LP_OK;
+  }
   S->slots.resize(o.slots);
   cudaError_t e = cudaSetDevice(S->base->device);
   const size_t ns = (size_t)o.max_batch_sources;
@@ -215,6 +509,26 @@ lp_status lp_serve_submit(lp_server* S, const int32_t* sources, int32_t n_src, l
   r->cap = degree_cap < 0 ? -1 : degree_cap;
   r->k = k;
   r->sources.assign(sources, sources + n_src);
+  if (S->opts.mode == 0) {
+    std::lock_guard<std::mutex> lock(S->mu);
+    DevLoop& D = S->dev;
+    if (S->closing) {
+      delete r;
+      return serve_fail(LP_EINVAL, "lp_serve_submit: server is closing");
+    }
+    if ((int64_t)(D.waiting.size() + D.inflight.size()) >= S->opts.max_pending) {
+      delete r;
+      return serve_fail(LP_EBUSY, "lp_serve_submit: queue full");
+    }
+    cudaSetDevice(S->base->device);
+    r->id = S->next_id++;
+    S->live[r->id] = r;
+    S->stats.submitted += 1;
+    *req_id = r->id;
+    D.waiting.push_back(r);
+    dev_harvest(S);  // frees finished requests' memory, admits in arrival order
+    return LP_OK;
+  }
   {
     std::lock_guard<std::mutex> lock(S->mu);
     if (S->closing) {
@@ -242,7 +556,19 @@ lp_status lp_serve_wait(lp_server* S, uint64_t req_id, int64_t timeout_us, lp_li
   auto it = S->live.find(req_id);
   if (it == S->live.end()) return serve_fail(LP_EINVAL, "lp_serve_wait: unknown request id");
   Request* r = it->second;
-  if (timeout_us < 0) {
+  if (S->opts.mode == 0) {
+    // poll: collect finished requests and keep the resident kernel running
+    cudaSetDevice(S->base->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+      dev_harvest(S);
+      if (r->done) break;
+      if (timeout_us >= 0 &&
+          std::chrono::steady_clock::now() - t0 >= std::chrono::microseconds(timeout_us))
+        return serve_fail(LP_ETIMEOUT, "lp_serve_wait: request not finished in time");
+      S->cv_done.wait_for(lock, std::chrono::microseconds(20), [&] { return r->done; });
+    }
+  } else if (timeout_us < 0) {
     S->cv_done.wait(lock, [&] { return r->done; });
   } else if (!S->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), [&] { return r->done; })) {
     return serve_fail(LP_ETIMEOUT, "lp_serve_wait: request not finished in time");
@@ -265,6 +591,10 @@ lp_status lp_serve_resume(lp_server* S) {
   {
     std::lock_guard<std::mutex> lock(S->mu);
     S->paused = false;
+    if (S->opts.mode == 0) {
+      cudaSetDevice(S->base->device);
+      dev_harvest(S);
+    }
   }
   S->cv_work.notify_all();
   return LP_OK;
@@ -275,6 +605,10 @@ lp_status lp_serve_poll(lp_server* S, uint64_t req_id, int32_t* done) {
   std::lock_guard<std::mutex> lock(S->mu);
   auto it = S->live.find(req_id);
   if (it == S->live.end()) return serve_fail(LP_EINVAL, "lp_serve_poll: unknown request id");
+  if (S->opts.mode == 0) {
+    cudaSetDevice(S->base->device);
+    dev_harvest(S);
+  }
   *done = it->second->done ? 1 : 0;
   return LP_OK;
 }
@@ -288,6 +622,29 @@ lp_status lp_serve_get_stats(lp_server* S, lp_serve_stats* out) {
 
 lp_status lp_serve_close(lp_server* S) {
   if (!S) return LP_OK;
+  if (S->opts.mode == 0) {
+    std::unique_lock<std::mutex> lock(S->mu);
+    cudaSetDevice(S->base->device);
+    S->closing = true;
+    S->paused = false;
+    DevLoop& D = S->dev;
+    for (;;) {  // finish every queued request
+      dev_harvest(S);
+      if (D.inflight.empty() && D.waiting.empty()) break;
+      if (__atomic_load_n(D.status, __ATOMIC_ACQUIRE) != 0) {
+        dev_harvest(S);  // fails the rest
+        if (D.inflight.empty()) break;
+      }
+      S->cv_done.wait_for(lock, std::chrono::microseconds(50));
+    }
+    __atomic_store_n(D.stop, 1u, __ATOMIC_RELEASE);  // idle CTAs leave at once
+    lock.unlock();
+    dev_free(D);
+    for (auto& kv : S->live) delete kv.second;
+    S->live.clear();
+    delete S;
+    return LP_OK;
+  }
   {
     std::lock_guard<std::mutex> lock(S->mu);
     S->closing = true;

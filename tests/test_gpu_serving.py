@@ -1,5 +1,9 @@
 """lp_serve_*: continuous batching of per-source queries (needs a GPU).
 
+Mode 0 (the default) serves requests with a resident kernel that claims one
+source at a time from a ring in mapped host memory; mode 1 runs batches from
+host worker threads.  Both modes are checked the same way.
+
 Each served result must equal lp_predict_sources on the same sources alone,
 whatever else is in the batch, and a quarter of the served requests (all four
 kinds of query) are checked row by row against the CPU oracle; requests of uneven sizes and different
@@ -39,7 +43,8 @@ def graph():
 KINDS = [("JC", 64, 10), ("RA", None, 5), ("CN", 16, 8), ("AA", 256, 10)]
 
 
-def test_served_equals_alone(lp, graph):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_served_equals_alone(lp, graph, mode):
     g = graph
     rng = np.random.default_rng(7)
     reqs = []
@@ -48,7 +53,7 @@ def test_served_equals_alone(lp, graph):
         reqs.append((rng.integers(0, g.n, n).astype(np.int32), KINDS[i % len(KINDS)]))
     with lp.Graph.from_csr(g) as G:
         expect = [G.predict_sources(kind[0], src, kind[2], kind[1]) for src, kind in reqs]
-        with lp.Server(G, slots=3, max_batch_sources=2000, max_k=16) as S:
+        with lp.Server(G, slots=3, max_batch_sources=2000, max_k=16, mode=mode) as S:
             ids = [None] * len(reqs)
 
             def submit(lo, hi):
@@ -78,11 +83,13 @@ def test_served_equals_alone(lp, graph):
             compare_sources(got[j][0], got[j][1], ol, oc, m, g, src, cap)
 
 
-def test_paused_timeout_full_queue_and_errors(lp, graph):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_paused_timeout_full_queue_and_errors(lp, graph, mode):
     g = graph
     src = np.arange(50, dtype=np.int32)
     with lp.Graph.from_csr(g) as G:
-        with lp.Server(G, slots=1, max_pending=3, max_batch_sources=100, paused=True) as S:
+        with lp.Server(G, slots=1, max_pending=3, max_batch_sources=100, paused=True,
+                       mode=mode) as S:
             a = S.submit(src, "JC", 10, 64)
             b = S.submit(src[:7], "JC", 10, 64)
             c = S.submit(src[:3], "RA", 5, None)
@@ -115,10 +122,50 @@ def test_paused_timeout_full_queue_and_errors(lp, graph):
         assert rc[0].tobytes() == ec[0].tobytes()
 
 
-def test_close_finishes_queued_requests(lp, graph):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_close_finishes_queued_requests(lp, graph, mode):
     g = graph
     with lp.Graph.from_csr(g) as G:
-        S = lp.Server(G, slots=2, paused=True)
+        S = lp.Server(G, slots=2, paused=True, mode=mode)
         for i in range(10):
             S.submit(np.arange(i * 10, i * 10 + 10, dtype=np.int32), "CN", 4)
         S.close()                                            # resumes, drains, frees
+
+
+def test_resident_kernel_leaves_when_idle_and_is_relaunched(lp, graph):
+    """The resident kernel's wait for work is bounded: with idle_polls = 20
+    (about 0.1 ms) it leaves between requests, and the next submitted request
+    launches it again; every result still equals the plain call."""
+    import time
+    g = graph
+    rng = np.random.default_rng(3)
+    with lp.Graph.from_csr(g) as G:
+        with lp.Server(G, slots=1, max_batch_sources=500, mode=0, idle_polls=20) as S:
+            for i in range(4):
+                src = rng.integers(0, g.n, 50 + 40 * i).astype(np.int32)
+                rid = S.submit(src, "RA", 10, 64)
+                got = S.wait(rid, 60_000_000)
+                exp = G.predict_sources("RA", src, 10, 64)
+                assert got[0].tobytes() == exp[0].tobytes()
+                assert np.array_equal(got[1], exp[1])
+                time.sleep(0.05)  # far longer than the kernel waits for work
+            st = S.stats()
+        assert st["kernel_launches"] >= 4 and st["completed"] == 4
+
+
+def test_resident_kernel_admits_by_memory(lp, graph):
+    """Room for 64 sources in flight (max_batch_sources 64, one slot): requests
+    of 40 sources are admitted one at a time as memory frees up, all finish
+    and equal the plain call."""
+    g = graph
+    rng = np.random.default_rng(4)
+    reqs = [rng.integers(0, g.n, 40).astype(np.int32) for _ in range(12)]
+    with lp.Graph.from_csr(g) as G:
+        with lp.Server(G, slots=1, max_batch_sources=64, max_k=8, mode=0) as S:
+            ids = [S.submit(r, "JC", 8, 64) for r in reqs]
+            got = [S.wait(i, 60_000_000) for i in ids]
+            st = S.stats()
+        assert st["max_batch_requests"] == 1  # two never fit at once
+        for r, (gl, gc) in zip(reqs, got):
+            el, ec = G.predict_sources("JC", r, 8, 64)
+            assert np.array_equal(gc, ec) and gl.tobytes() == el.tobytes()
