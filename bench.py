@@ -465,52 +465,63 @@ def run_serve(args):
             G.predict_sources(measure, r, k, cap)
             lat_p[i] = (time.perf_counter() - t_start) - arr[i]
         span_p = time.perf_counter() - t_start
-        # served: submit at arrival times, several waiters
-        S = lp.Server(G, slots=args.slots, max_batch_sources=65536, max_k=16)
-        ids = [None] * R
-        lat_s = np.zeros(R)
-        got = [None] * R
-        ready = [threading.Event() for _ in range(R)]
-        t_start = time.perf_counter()
-
-        def submitter():
-            for i, r in enumerate(reqs):
-                now = time.perf_counter() - t_start
-                if now < arr[i]:
-                    time.sleep(arr[i] - now)
-                ids[i] = S.submit(r, measure, k, cap)
-                ready[i].set()
-
-        def waiter(j, nw):
-            for i in range(j, R, nw):
-                ready[i].wait()
-                got[i] = S.wait(ids[i], -1)
-                lat_s[i] = (time.perf_counter() - t_start) - arr[i]
-
-        nw = 8
-        th = [threading.Thread(target=submitter)] + \
-             [threading.Thread(target=waiter, args=(j, nw)) for j in range(nw)]
-        for t in th:
-            t.start()
-        for t in th:
-            t.join()
-        span_s = time.perf_counter() - t_start
-        st = S.stats()
-        S.close()
-        same = all(got[i][0].tobytes() == plain_res[i][0].tobytes() and
-                   np.array_equal(got[i][1], plain_res[i][1]) for i in range(R))
-        out["loads"].append({
-            "load": rho, "arrival_req_per_s": round(lam, 1),
-            "plain": {"p50_ms": round(1e3 * float(np.percentile(lat_p, 50)), 2),
-                      "p99_ms": round(1e3 * float(np.percentile(lat_p, 99)), 2),
-                      "edges_per_s": round(edges / span_p, 1)},
-            "served": {"p50_ms": round(1e3 * float(np.percentile(lat_s, 50)), 2),
-                       "p99_ms": round(1e3 * float(np.percentile(lat_s, 99)), 2),
-                       "edges_per_s": round(edges / span_s, 1),
-                       "batches": st["batches"], "max_batch_requests": st["max_batch_requests"]},
-            "identical_to_plain": bool(same)})
+        entry = {"load": rho, "arrival_req_per_s": round(lam, 1),
+                 "plain": {"p50_ms": round(1e3 * float(np.percentile(lat_p, 50)), 2),
+                           "p99_ms": round(1e3 * float(np.percentile(lat_p, 99)), 2),
+                           "edges_per_s": round(edges / span_p, 1)}}
+        for mode in (0, 1):
+            entry["served" if mode == 0 else "served_host_batches"] = serve_once(
+                lp, G, reqs, arr, plain_res, measure, k, cap, mode, args.slots, edges)
+        out["loads"].append(entry)
     G.close()
     return out
+
+
+def serve_once(lp, G, reqs, arr, plain_res, measure, k, cap, mode, slots, edges):
+    """Submit every request at its arrival time to a server of the given mode
+    (0: resident kernel, 1: host batches), wait from several threads; latency
+    is completion minus arrival."""
+    import threading
+    R = len(reqs)
+    S = lp.Server(G, slots=slots, max_batch_sources=65536, max_k=16, mode=mode)
+    ids = [None] * R
+    lat_s = np.zeros(R)
+    got = [None] * R
+    ready = [threading.Event() for _ in range(R)]
+    t_start = time.perf_counter()
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            now = time.perf_counter() - t_start
+            if now < arr[i]:
+                time.sleep(arr[i] - now)
+            ids[i] = S.submit(r, measure, k, cap)
+            ready[i].set()
+
+    def waiter(j, nw):
+        for i in range(j, R, nw):
+            ready[i].wait()
+            got[i] = S.wait(ids[i], -1)
+            lat_s[i] = (time.perf_counter() - t_start) - arr[i]
+
+    nw = 8
+    th = [threading.Thread(target=submitter)] + \
+         [threading.Thread(target=waiter, args=(j, nw)) for j in range(nw)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    span_s = time.perf_counter() - t_start
+    st = S.stats()
+    S.close()
+    same = all(got[i][0].tobytes() == plain_res[i][0].tobytes() and
+               np.array_equal(got[i][1], plain_res[i][1]) for i in range(R))
+    return {"p50_ms": round(1e3 * float(np.percentile(lat_s, 50)), 2),
+            "p99_ms": round(1e3 * float(np.percentile(lat_s, 99)), 2),
+            "edges_per_s": round(edges / span_s, 1),
+            "batches": st["batches"], "max_batch_requests": st["max_batch_requests"],
+            "kernel_launches": st["kernel_launches"],
+            "identical_to_plain": bool(same)}
 
 
 # ------------------------------------------------------- reference arm ----

@@ -158,12 +158,11 @@ __device__ __forceinline__ u32 pair_hash(int b) {
 
 // One group at a time per CTA (claimed from *claim): the marked set is Gamma_u
 // (b with |Gamma_b| <= cap); every link (u, v) of the group counts the marked
-// entries of Gamma_v (a warp per link).  The set is a bitmap over every id: in
-// shared memory when the ids fit (nwords words), else the CTA's slice of a
-// device bitmap of gwords words, marked with L2 atomics and read through the
-// L2; when the ids do not fit in shared memory, a group whose Gamma_u is short
-// uses a hash set of its entries (keys b + 1, 0 = empty) in shared memory
-// instead.  *ngroups is the total the scan left after the last vertex.
+// entries of Gamma_v (a warp per link).  The set is a bitmap over the ids
+// [w0, w0 + 32 * nwords): over all vertices when they fit, else one window of
+// ids at a time; a group whose Gamma_u is short uses a hash set of its
+// entries (keys b + 1, 0 = empty) in the same shared memory instead.
+// *ngroups is the total the scan left after the last vertex.
 __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict__ links,
                                                             const int* __restrict__ perm,
                                                             const int4* __restrict__ groups,
@@ -173,13 +172,13 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
                                                             const Arc* __restrict__ arc, int cap,
                                                             int nwords, int n,
                                                             u32* __restrict__ claim,
-                                                            u32* __restrict__ gbits,
-                                                            int gwords) {
+                                                            int* __restrict__ cur) {
   extern __shared__ u32 bits[];
   __shared__ u32 s_g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const u32 ngroups = (u32)total->y;
-  const bool one_window = n <= nwords * 32;
+  const int width = nwords * 32;
+  const bool one_window = n <= width;
   for (int i = threadIdx.x; i < nwords; i += blockDim.x) bits[i] = 0;
   for (;;) {
     if (threadIdx.x == 0) s_g = atomicAdd(claim, 1u);
@@ -220,83 +219,92 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
       __syncthreads();
       continue;
     }
-    // a bitmap of Gamma_u over every id: in shared memory when the ids fit,
-    // else this CTA's slice of a device bitmap (read through the L2 cache)
-    u32* bm = one_window ? bits : gbits + (size_t)blockIdx.x * (size_t)gwords;
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const int b = __ldg(idx + e);
-      if (arc[e].z <= cap) atomicOr(&bm[b >> 5], 1u << (b & 31));
-    }
-    __syncthreads();
-    for (int j = wid; j < G.z; j += nw) {  // warp-uniform trips
-      const int li = perm[G.y + j];
-      const lp_link L = links[li];
-      const int v = L.u == u ? L.v : L.u;
-      int c = 0;
-      const int vs = off[v], ve = off[v + 1];
-      int e = vs + lane;
-      if (one_window) {
-        for (; e + 96 < ve; e += 128) {  // four loads in flight per lane
-          const int b0 = __ldg(idx + e), b1 = __ldg(idx + e + 32), b2 = __ldg(idx + e + 64),
-                    b3 = __ldg(idx + e + 96);
-          c += ((bm[b0 >> 5] >> (b0 & 31)) & 1u) + ((bm[b1 >> 5] >> (b1 & 31)) & 1u) +
-               ((bm[b2 >> 5] >> (b2 & 31)) & 1u) + ((bm[b3 >> 5] >> (b3 & 31)) & 1u);
+    for (int w0 = 0; w0 < n; w0 += width) {  // one pass when the bitmap covers every id
+      const int w1 = min(n, w0 + width);
+      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int b = __ldg(idx + e);
+        if (b < w0 || b >= w1) continue;
+        if (arc[e].z <= cap) atomicOr(&bits[(b - w0) >> 5], 1u << ((b - w0) & 31));
+      }
+      __syncthreads();
+      for (int j = wid; j < G.z; j += nw) {  // warp-uniform trips
+        const int li = perm[G.y + j];
+        const lp_link L = links[li];
+        const int v = L.u == u ? L.v : L.u;
+        int c = 0;
+        const int vs = off[v], ve = off[v + 1];
+        // Gamma_v is sorted and the windows ascend: this window's entries
+        // start where the previous window's ended (a cursor per link), and
+        // end at the first entry >= w1, found by the walk itself
+        if (one_window) {  // every id in the bitmap: the whole list, no bound
+          int e = vs + lane;
+          for (; e + 96 < ve; e += 128) {  // four loads in flight per lane
+            const int b0 = __ldg(idx + e), b1 = __ldg(idx + e + 32), b2 = __ldg(idx + e + 64),
+                      b3 = __ldg(idx + e + 96);
+            c += ((bits[b0 >> 5] >> (b0 & 31)) & 1u) + ((bits[b1 >> 5] >> (b1 & 31)) & 1u) +
+                 ((bits[b2 >> 5] >> (b2 & 31)) & 1u) + ((bits[b3 >> 5] >> (b3 & 31)) & 1u);
+          }
+          for (; e < ve; e += 32) {
+            const int b = __ldg(idx + e);
+            c += (bits[b >> 5] >> (b & 31)) & 1u;
+          }
+          c = __reduce_add_sync(FULLMASK, (u32)c);
+          if (lane == 0) links[li].cn = c;
+          continue;
         }
-        for (; e < ve; e += 32) {
-          const int b = __ldg(idx + e);
-          c += (bm[b >> 5] >> (b & 31)) & 1u;
+        int e0 = w0 == 0 ? vs : cur[G.y + j];
+        int next = ve;
+        for (;;) {  // warp-uniform trips; four loads in flight per lane
+          int bb[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int e = e0 + 32 * k + lane;
+            bb[k] = e < ve ? __ldg(idx + e) : INT_MAX;
+          }
+          bool stop = false;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const bool in = bb[k] < w1;
+            const int b = bb[k] - w0;
+            c += in ? ((bits[b >> 5] >> (b & 31)) & 1u) : 0u;
+            const u32 m = __ballot_sync(FULLMASK, !in);
+            if (m) {  // warp-uniform
+              next = e0 + 32 * k + __ffs(m) - 1;
+              stop = true;
+              break;
+            }
+          }
+          if (stop) break;
+          e0 += 128;
         }
-      } else {  // the marks were made by L2 atomics: read them from the L2
-        for (; e + 96 < ve; e += 128) {
-          const int b0 = __ldg(idx + e), b1 = __ldg(idx + e + 32), b2 = __ldg(idx + e + 64),
-                    b3 = __ldg(idx + e + 96);
-          const u32 m0 = __ldcg(bm + (b0 >> 5)), m1 = __ldcg(bm + (b1 >> 5)),
-                    m2 = __ldcg(bm + (b2 >> 5)), m3 = __ldcg(bm + (b3 >> 5));
-          c += ((m0 >> (b0 & 31)) & 1u) + ((m1 >> (b1 & 31)) & 1u) + ((m2 >> (b2 & 31)) & 1u) +
-               ((m3 >> (b3 & 31)) & 1u);
-        }
-        for (; e < ve; e += 32) {
-          const int b = __ldg(idx + e);
-          c += (__ldcg(bm + (b >> 5)) >> (b & 31)) & 1u;
+        c = __reduce_add_sync(FULLMASK, (u32)c);
+        if (lane == 0) {
+          cur[G.y + j] = min(next, ve);
+          if (w0 == 0) links[li].cn = c;
+          else links[li].cn += c;
         }
       }
-      c = __reduce_add_sync(FULLMASK, (u32)c);
-      if (lane == 0) links[li].cn = c;
+      __syncthreads();
+      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int b = __ldg(idx + e);
+        if (b >= w0 && b < w1) bits[(b - w0) >> 5] = 0;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) bm[__ldg(idx + e) >> 5] = 0;
-    __syncthreads();
   }
 }
 
 // Scratch layout: sc int2[n + 1], cnt int[n + 1], perm int[links], groups
-// int4[n], sums int2[chunks], claim u32, and (ids beyond a shared-memory
-// bitmap) a bitmap of every id per SM; every part 256-byte aligned (groups
-// are written as int4).
+// int4[n], sums int2[chunks], claim u32, window cursors int[links]; every
+// part 256-byte aligned (groups are written as int4).
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-constexpr int kSmemBitmapWords = 224 * 1024 / 4;
-
-static int pair_num_sms() {
-  int dev = 0, nsm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  return nsm > 0 ? nsm : 1;
-}
-
-// The per-SM device bitmaps, when the ids do not fit a shared-memory one.
-static size_t global_bitmap_bytes(int n) {
-  const size_t words = ((size_t)n + 31) / 32;
-  if (words <= (size_t)kSmemBitmapWords) return 0;
-  return align256(words * 4) * (size_t)pair_num_sms();
-}
 
 size_t pair_groups_scratch(int n, u64 nlinks) {
   const size_t n1 = (size_t)n + 1;
   return align256(n1 * sizeof(int2)) + align256(n1 * sizeof(int)) + align256(nlinks * sizeof(int)) +
          align256((size_t)n * sizeof(int4)) +
          align256(((n1 + kScanChunk - 1) / kScanChunk) * sizeof(int2)) + 256 +
-         global_bitmap_bytes(n);
+         align256(nlinks * sizeof(int));
 }
 
 // Counts of links[0, n), grouped by the endpoint of larger degree; scratch of pair_groups_scratch bytes.
@@ -319,11 +327,8 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
   p += align256((size_t)nb * sizeof(int2));
   u32* claim = reinterpret_cast<u32*>(p);
   p += 256;
-  u32* gbits = reinterpret_cast<u32*>(p);
-  const size_t gbytes = global_bitmap_bytes(nv);
-  const int gwords = gbytes ? (int)(align256((((size_t)nv + 31) / 32) * 4) / 4) : 0;
+  int* cur = reinterpret_cast<int*>(p);
   cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)n1 * sizeof(int), st);
-  if (e == cudaSuccess && gbytes) e = cudaMemsetAsync(gbits, 0, gbytes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(claim, 0, sizeof(u32), st);
   if (e != cudaSuccess) return e;
   const int gb = (int)std::min<u64>((n + 255) / 256, 152 * 8);
@@ -335,14 +340,16 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
   k_pair_scatter<<<gb, 256, 0, st>>>(links, n, off, sc, perm);
   // a bitmap over every vertex when it fits in 224 KB, else windows of that
   // size (and room for the hash set)
-  const int nwords = std::max(1 << kPairHashLog, std::min((nv + 31) / 32, kSmemBitmapWords));
+  const int nwords = std::max(1 << kPairHashLog, std::min((nv + 31) / 32, 224 * 1024 / 4));
   const size_t smem = (size_t)nwords * 4;
   e = cudaFuncSetAttribute(k_pair_cn_groups, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            224 * 1024);
   if (e != cudaSuccess) return e;
-  const int nsm = pair_num_sms();
+  int dev = 0, nsm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   k_pair_cn_groups<<<nsm, 1024, smem, st>>>(links, perm, groups, sc + nv, off, idx, arc, cap,
-                                            nwords, nv, claim, gbits, gwords);
+                                            nwords, nv, claim, cur);
   if (launches) *launches += 7;
   return cudaGetLastError();
 }
