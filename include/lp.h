@@ -348,7 +348,10 @@ typedef struct {
                                 1: host worker threads run batches               */
   int32_t idle_polls;        /* mode 0: polls (about 4 us apart) a resident CTA
                                 waits for work before it leaves (0: 2500)        */
-  int32_t reserved;
+  int32_t defer_wedges;      /* mode 0: a source with more wedges than this (its
+                                hub-limited two-hop work) is not counted by the
+                                resident kernel but by the tiered per-source
+                                pipeline when its request is collected (0: 65536) */
 } lp_serve_opts;
 
 typedef struct {
@@ -361,6 +364,8 @@ typedef struct {
   int64_t kernel_launches;   /* mode 0: launches of the resident kernel (it leaves
                                 after idle_polls polls without work and is
                                 launched again when work arrives)                */
+  int64_t deferred_sources;  /* mode 0: sources counted by the tiered pipeline
+                                (more than defer_wedges wedges)                   */
 } lp_serve_stats;
 
 /* Start a server on graph g (which must outlive it).  opts may be NULL.

@@ -55,13 +55,14 @@ class lp_serve_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("max_batch_sources", ctypes.c_int32),
                 ("max_pending", ctypes.c_int32), ("max_k", ctypes.c_int32),
                 ("paused", ctypes.c_int32), ("mode", ctypes.c_int32),
-                ("idle_polls", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("idle_polls", ctypes.c_int32), ("defer_wedges", ctypes.c_int32)]
 
 
 class lp_serve_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("batched_sources", ctypes.c_int64),
-                ("max_batch_requests", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+                ("max_batch_requests", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("deferred_sources", ctypes.c_int64)]
 
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -465,9 +466,9 @@ class Server:
     resident kernel; mode 1: host worker threads running batches)."""
 
     def __init__(self, graph, slots=0, max_batch_sources=0, max_pending=0, max_k=0,
-                 paused=False, mode=0, idle_polls=0):
+                 paused=False, mode=0, idle_polls=0, defer_wedges=0):
         o = lp_serve_opts(slots, max_batch_sources, max_pending, max_k, 1 if paused else 0, mode,
-                          idle_polls)
+                          idle_polls, defer_wedges)
         h = _vp()
         _check(_load().lp_serve_open(graph.handle if isinstance(graph, Graph) else graph,
                                      ctypes.byref(o), ctypes.byref(h)))

@@ -306,6 +306,8 @@ struct SrvArgs {
   unsigned* done;                     // completion word per slot (host memory)
   unsigned* status;                   // device error word (host memory)
   const unsigned* stop;               // 1: leave at once when idle (host memory)
+  unsigned char* defer;               // per pool source: 1 = left to the host (host memory)
+  unsigned long long defer_wedges;    // sources with more wedges are deferred
 };
 size_t serve_smem_bytes(int max_k);
 cudaError_t launch_serve(const SrvArgs& S, int max_k, cudaStream_t st);

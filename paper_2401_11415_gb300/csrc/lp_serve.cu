@@ -104,6 +104,14 @@ struct DevLoop {
   unsigned* done = nullptr;
   unsigned* status = nullptr;
   unsigned* stop = nullptr;
+  unsigned char* defer = nullptr;  // per pool source: left to the host
+  lp::Graph* shadow = nullptr;     // the tiered pipeline for deferred sources
+  int* d_dsrc = nullptr;
+  lp_link* d_dout = nullptr;
+  int* d_dcnt = nullptr;
+  std::vector<int> h_dsrc;
+  std::vector<lp_link> h_dout;
+  std::vector<int> h_dcnt;
   unsigned long long* d_head = nullptr;
   unsigned long long* d_finished = nullptr;
   long long pool_cap = 0;        // sources the pools hold
@@ -249,6 +257,11 @@ void dev_free(DevLoop& D) {
   cudaFreeHost(D.done);
   cudaFreeHost(D.status);
   cudaFreeHost(D.stop);
+  cudaFreeHost(D.defer);
+  cudaFree(D.d_dsrc);
+  cudaFree(D.d_dout);
+  cudaFree(D.d_dcnt);
+  if (D.shadow) lp::destroy_shadow(D.shadow);
   cudaFree(D.d_head);
   cudaFree(D.d_finished);
   D = DevLoop();
@@ -276,6 +289,7 @@ cudaError_t dev_open(lp_server* S) {
   int* src_d = nullptr;
   lp_link* out_d = nullptr;
   unsigned *done_d = nullptr, *status_d = nullptr, *stop_d = nullptr;
+  unsigned char* defer_d = nullptr;
   cudaError_t e = mapped(&D.ring, (size_t)D.ring_cap, &ring_d);
   if (e == cudaSuccess) e = mapped(&D.tail, 1, &tail_d);
   if (e == cudaSuccess) e = mapped(&D.reqs, (size_t)D.nslots, &reqs_d);
@@ -284,6 +298,12 @@ cudaError_t dev_open(lp_server* S) {
   if (e == cudaSuccess) e = mapped(&D.done, (size_t)D.nslots, &done_d);
   if (e == cudaSuccess) e = mapped(&D.status, 1, &status_d);
   if (e == cudaSuccess) e = mapped(&D.stop, 1, &stop_d);
+  if (e == cudaSuccess) e = mapped(&D.defer, (size_t)D.pool_cap, &defer_d);
+  const size_t nd = (size_t)S->opts.max_batch_sources;
+  if (e == cudaSuccess) e = cudaMalloc(&D.d_dsrc, sizeof(int) * nd);
+  if (e == cudaSuccess) e = cudaMalloc(&D.d_dout, sizeof(lp_link) * nd * S->opts.max_k);
+  if (e == cudaSuccess) e = cudaMalloc(&D.d_dcnt, sizeof(int) * nd);
+  if (e == cudaSuccess && lp::make_shadow(g, &D.shadow) != LP_OK) e = cudaErrorMemoryAllocation;
   if (e == cudaSuccess) e = cudaMalloc(&D.d_head, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&D.d_finished, sizeof(unsigned long long) * D.nslots);
   if (e == cudaSuccess) e = cudaMemset(D.d_head, 0, sizeof(unsigned long long));
@@ -311,6 +331,8 @@ cudaError_t dev_open(lp_server* S) {
   A.done = done_d;
   A.status = status_d;
   A.stop = stop_d;
+  A.defer = defer_d;
+  A.defer_wedges = (unsigned long long)S->opts.defer_wedges;
   D.slot_total.assign(D.nslots, 0);
   D.free_slots.clear();
   for (int i = D.nslots - 1; i >= 0; --i) D.free_slots.push_back(i);
@@ -404,13 +426,54 @@ void dev_harvest(lp_server* S) {
       r->out.resize(n * k);
       r->counts.resize(n);
       const lp_link* base = D.out_pool + (size_t)r->off * S->opts.max_k;
+      D.h_dsrc.clear();
       for (size_t j = 0; j < n; ++j) {
+        if (D.defer[r->off + j]) {  // left to the tiered pipeline below
+          D.defer[r->off + j] = 0;
+          D.h_dsrc.push_back((int)j);
+          continue;
+        }
         std::memcpy(r->out.data() + j * k, base + j * k, sizeof(lp_link) * k);
         int c = 0;
         while (c < (int)k && r->out[j * k + c].v >= 0) ++c;
         r->counts[j] = c;
       }
       r->status = LP_OK;
+      if (!D.h_dsrc.empty()) {
+        const int nd = (int)D.h_dsrc.size();
+        std::vector<int> srcs(nd);
+        for (int q = 0; q < nd; ++q) srcs[q] = r->sources[D.h_dsrc[q]];
+        D.h_dout.resize((size_t)nd * k);
+        D.h_dcnt.resize(nd);
+        cudaStream_t ds = D.shadow->stream;
+        cudaError_t e = cudaMemcpyAsync(D.d_dsrc, srcs.data(), sizeof(int) * nd,
+                                        cudaMemcpyHostToDevice, ds);
+        lp_status ps = e == cudaSuccess ? LP_OK : lp::report_cuda(e, "serving: deferred sources");
+        if (ps == LP_OK)
+          ps = lp::run_sources_dev(*D.shadow, r->measure, r->cap, D.d_dsrc, nd, r->k, 0.0,
+                                   D.d_dout, D.d_dcnt);
+        if (ps == LP_OK) {
+          e = cudaMemcpyAsync(D.h_dout.data(), D.d_dout, sizeof(lp_link) * nd * k,
+                              cudaMemcpyDeviceToHost, ds);
+          if (e == cudaSuccess)
+            e = cudaMemcpyAsync(D.h_dcnt.data(), D.d_dcnt, sizeof(int) * nd, cudaMemcpyDeviceToHost,
+                                ds);
+          if (e == cudaSuccess) e = cudaStreamSynchronize(ds);
+          if (e != cudaSuccess) ps = lp::report_cuda(e, "serving: deferred rows");
+        }
+        if (ps == LP_OK) {
+          for (int q = 0; q < nd; ++q) {
+            const size_t j = (size_t)D.h_dsrc[q];
+            std::memcpy(r->out.data() + j * k, D.h_dout.data() + (size_t)q * k,
+                        sizeof(lp_link) * k);
+            r->counts[j] = D.h_dcnt[q];
+          }
+          S->stats.deferred_sources += nd;
+        } else {
+          r->status = ps;
+          r->error = lp_last_error();
+        }
+      }
     } else {
       r->status = st == 2 ? LP_ECUDA : LP_EINTERNAL;
       r->error = st == 2 ? "the resident serving kernel failed" : "serving: device check failed";
@@ -446,8 +509,10 @@ lp_status lp_serve_open(const lp_graph* g, const lp_serve_opts* opts, lp_server*
   if (o.max_pending == 0) o.max_pending = 65536;
   if (o.max_k == 0) o.max_k = 16;
   if (o.idle_polls == 0) o.idle_polls = 2500;
+  if (o.defer_wedges == 0) o.defer_wedges = 65536;
   if (o.slots < 1 || o.slots > 8 || o.max_batch_sources < 1 || o.max_pending < 1 || o.max_k < 1 ||
-      o.max_k > LP_MAX_TOPK_PER_SOURCE || o.mode < 0 || o.mode > 1 || o.idle_polls < 1)
+      o.max_k > LP_MAX_TOPK_PER_SOURCE || o.mode < 0 || o.mode > 1 || o.idle_polls < 1 ||
+      o.defer_wedges < 1)
     return serve_fail(LP_EINVAL, "lp_serve_open: option out of range");
   lp_server* S = new (std::nothrow) lp_server();
   if (!S) return serve_fail(LP_ENOMEM, "lp_serve_open: host allocation");

@@ -45,8 +45,10 @@ __device__ __forceinline__ void st_release_sys(unsigned* p, unsigned v) {
 }
 
 // One source: its k best partners into row[0, k) (fillers after the count).
+// Returns false, writing nothing, for a source with more than defer_wedges
+// wedges (the host counts it with the tiered pipeline).
 template <typename V>
-__device__ void serve_source(const SrvArgs& S, const SrvReq& R, int a, lp_link* row,
+__device__ bool serve_source(const SrvArgs& S, const SrvReq& R, int a, lp_link* row,
                              unsigned char* smem, TopEnt* tops) {
   int* keys = reinterpret_cast<int*>(smem);
   V* vals = reinterpret_cast<V*>(smem + (size_t)kSrvSlots * 4);
@@ -90,6 +92,7 @@ __device__ void serve_source(const SrvArgs& S, const SrvReq& R, int a, lp_link* 
   if (lane == 0 && w) atomicAdd(&s_w, w);
   __syncthreads();
   const u64 W = s_w;
+  if (W > S.defer_wedges) return false;  // CTA-uniform
   TopEnt* top = tops + wid * R.k;
   int tcnt = 0;
   u64 n_cand = 0;
@@ -219,6 +222,7 @@ __device__ void serve_source(const SrvArgs& S, const SrvReq& R, int a, lp_link* 
     if (lane == 0) row[j] = L;
   }
   __syncthreads();
+  return true;
 }
 
 // The resident kernel: claim work items {request slot, source index} until
@@ -272,11 +276,11 @@ __global__ void __launch_bounds__(kSrvThreads, 2) k_serve(SrvArgs S) {
     const SrvReq R = s_req;
     const int a = *(const volatile int*)(S.src_pool + R.src_off + it.y);
     lp_link* row = S.out_pool + R.out_off + (long long)it.y * R.k;
-    if (R.measure == LP_AA || R.measure == LP_RA)
-      serve_source<u64>(S, R, a, row, smem, tops);
-    else
-      serve_source<u32>(S, R, a, row, smem, tops);
+    const bool ok = (R.measure == LP_AA || R.measure == LP_RA)
+                        ? serve_source<u64>(S, R, a, row, smem, tops)
+                        : serve_source<u32>(S, R, a, row, smem, tops);
     if (threadIdx.x == 0) {
+      if (!ok) *(volatile unsigned char*)(S.defer + R.src_off + it.y) = 1;
       __threadfence_system();  // the row is visible before the count and the flag
       const unsigned long long old = atomicAdd(S.finished + it.x, 1ull);
       if ((long long)old + 1 == R.target) st_release_sys(S.done + it.x, R.seq);

@@ -169,3 +169,23 @@ def test_resident_kernel_admits_by_memory(lp, graph):
         for r, (gl, gc) in zip(reqs, got):
             el, ec = G.predict_sources("JC", r, 8, 64)
             assert np.array_equal(gc, ec) and gl.tobytes() == el.tobytes()
+
+
+@pytest.mark.parametrize("measure,cap", [("RA", None), ("JC", 64)])
+def test_resident_kernel_defers_large_sources(lp, graph, measure, cap):
+    """Sources with more wedges than defer_wedges (here 200, so many of them)
+    are left by the resident kernel to the tiered per-source pipeline when the
+    request is collected; the rows are the plain call's either way."""
+    g = graph
+    rng = np.random.default_rng(9)
+    reqs = [rng.integers(0, g.n, m).astype(np.int32) for m in (1, 17, 300, 900)]
+    with lp.Graph.from_csr(g) as G:
+        with lp.Server(G, slots=2, max_batch_sources=1000, max_k=10, mode=0,
+                       defer_wedges=200) as S:
+            ids = [S.submit(r, measure, 10, cap) for r in reqs]
+            got = [S.wait(i, 60_000_000) for i in ids]
+            st = S.stats()
+        assert 0 < st["deferred_sources"] < sum(len(r) for r in reqs)
+        for r, (gl, gc) in zip(reqs, got):
+            el, ec = G.predict_sources(measure, r, 10, cap)
+            assert np.array_equal(gc, ec) and gl.tobytes() == el.tobytes()
