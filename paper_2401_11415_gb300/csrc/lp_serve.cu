@@ -55,6 +55,7 @@ struct Request {
   int slot = -1;
   long long off = 0;  // first source in the pools
   unsigned seq = 0;
+  std::vector<int> deferred;  // rows left to the tiered pipeline
 };
 
 // First-fit allocator of [0, cap) ranges (pool entries).
@@ -123,6 +124,9 @@ struct DevLoop {
   RangeAlloc pool;
   std::deque<Request*> waiting;  // submitted, not admitted yet
   std::vector<Request*> inflight;
+  std::deque<Request*> dq;        // waiting for their deferred rows
+  std::thread dthread;            // runs the deferred rows in batches
+  bool dstop = false;             // ends dthread (set after the last request)
   bool running = false;
   unsigned next_seq = 1;
 };
@@ -243,6 +247,8 @@ void worker_main(lp_server* S, int si) {
 lp_status serve_fail(lp_status s, const char* msg) { return lp::report_error(s, msg); }
 
 // ------------------------------------------------------------ mode 0 ----
+
+int first_k(const std::vector<Request*>& batch) { return batch.empty() ? 1 : batch[0]->k; }
 
 void dev_free(DevLoop& D) {
   if (D.stream) {
@@ -408,6 +414,85 @@ bool dev_admit(lp_server* S, Request* r) {
   return true;
 }
 
+// The deferred rows: requests whose device part is collected wait in D.dq;
+// this thread takes every waiting request of the first one's (measure, hub
+// limit, k), up to max_batch_sources deferred sources, runs them as one
+// tiered per-source batch (lp_predict_sources semantics) and completes them.
+void dev_deferred_main(lp_server* S) {
+  DevLoop& D = S->dev;
+  cudaSetDevice(S->base->device);
+  std::vector<Request*> batch;
+  std::vector<int> srcs;
+  for (;;) {
+    batch.clear();
+    srcs.clear();
+    {
+      std::unique_lock<std::mutex> lock(S->mu);
+      S->cv_work.wait(lock, [&] { return D.dstop || !D.dq.empty(); });
+      if (D.dq.empty()) return;  // stopped and drained
+      Request* first = D.dq.front();
+      for (auto it = D.dq.begin(); it != D.dq.end();) {
+        Request* r = *it;
+        if (r->measure == first->measure && r->cap == first->cap && r->k == first->k &&
+            (batch.empty() || srcs.size() + r->deferred.size() <=
+                                  (size_t)S->opts.max_batch_sources)) {
+          for (int j : r->deferred) srcs.push_back(r->sources[j]);
+          batch.push_back(r);
+          it = D.dq.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    const int nd = (int)srcs.size(), k = first_k(batch);
+    D.h_dout.resize((size_t)nd * k);
+    D.h_dcnt.resize(nd);
+    cudaStream_t ds = D.shadow->stream;
+    lp_status ps = LP_OK;
+    for (int at = 0; at < nd && ps == LP_OK; at += S->opts.max_batch_sources) {
+      const int m = std::min(nd - at, S->opts.max_batch_sources);
+      cudaError_t e = cudaMemcpyAsync(D.d_dsrc, srcs.data() + at, sizeof(int) * m,
+                                      cudaMemcpyHostToDevice, ds);
+      if (e != cudaSuccess) ps = lp::report_cuda(e, "serving: deferred sources");
+      if (ps == LP_OK)
+        ps = lp::run_sources_dev(*D.shadow, batch[0]->measure, batch[0]->cap, D.d_dsrc, m, k, 0.0,
+                                 D.d_dout, D.d_dcnt);
+      if (ps == LP_OK) {
+        e = cudaMemcpyAsync(D.h_dout.data() + (size_t)at * k, D.d_dout, sizeof(lp_link) * m * k,
+                            cudaMemcpyDeviceToHost, ds);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(D.h_dcnt.data() + at, D.d_dcnt, sizeof(int) * m,
+                              cudaMemcpyDeviceToHost, ds);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ds);
+        if (e != cudaSuccess) ps = lp::report_cuda(e, "serving: deferred rows");
+      }
+    }
+    const std::string error = ps == LP_OK ? std::string() : std::string(lp_last_error());
+    {
+      std::lock_guard<std::mutex> lock(S->mu);
+      int q = 0;
+      for (Request* r : batch) {
+        for (int j : r->deferred) {
+          if (ps == LP_OK) {
+            std::memcpy(r->out.data() + (size_t)j * k, D.h_dout.data() + (size_t)q * k,
+                        sizeof(lp_link) * k);
+            r->counts[j] = D.h_dcnt[q];
+          }
+          ++q;
+        }
+        if (ps != LP_OK) {
+          r->status = ps;
+          r->error = error;
+        }
+        r->done = true;
+        S->stats.completed += 1;
+      }
+      S->stats.deferred_sources += nd;
+    }
+    S->cv_done.notify_all();
+  }
+}
+
 // Collect finished requests (copy their rows out, free their memory), then
 // admit waiting requests in arrival order while they fit.
 void dev_harvest(lp_server* S) {
@@ -426,11 +511,11 @@ void dev_harvest(lp_server* S) {
       r->out.resize(n * k);
       r->counts.resize(n);
       const lp_link* base = D.out_pool + (size_t)r->off * S->opts.max_k;
-      D.h_dsrc.clear();
+      r->deferred.clear();
       for (size_t j = 0; j < n; ++j) {
-        if (D.defer[r->off + j]) {  // left to the tiered pipeline below
+        if (D.defer[r->off + j]) {  // left to the tiered pipeline (dev_deferred_main)
           D.defer[r->off + j] = 0;
-          D.h_dsrc.push_back((int)j);
+          r->deferred.push_back((int)j);
           continue;
         }
         std::memcpy(r->out.data() + j * k, base + j * k, sizeof(lp_link) * k);
@@ -439,46 +524,17 @@ void dev_harvest(lp_server* S) {
         r->counts[j] = c;
       }
       r->status = LP_OK;
-      if (!D.h_dsrc.empty()) {
-        const int nd = (int)D.h_dsrc.size();
-        std::vector<int> srcs(nd);
-        for (int q = 0; q < nd; ++q) srcs[q] = r->sources[D.h_dsrc[q]];
-        D.h_dout.resize((size_t)nd * k);
-        D.h_dcnt.resize(nd);
-        cudaStream_t ds = D.shadow->stream;
-        cudaError_t e = cudaMemcpyAsync(D.d_dsrc, srcs.data(), sizeof(int) * nd,
-                                        cudaMemcpyHostToDevice, ds);
-        lp_status ps = e == cudaSuccess ? LP_OK : lp::report_cuda(e, "serving: deferred sources");
-        if (ps == LP_OK)
-          ps = lp::run_sources_dev(*D.shadow, r->measure, r->cap, D.d_dsrc, nd, r->k, 0.0,
-                                   D.d_dout, D.d_dcnt);
-        if (ps == LP_OK) {
-          e = cudaMemcpyAsync(D.h_dout.data(), D.d_dout, sizeof(lp_link) * nd * k,
-                              cudaMemcpyDeviceToHost, ds);
-          if (e == cudaSuccess)
-            e = cudaMemcpyAsync(D.h_dcnt.data(), D.d_dcnt, sizeof(int) * nd, cudaMemcpyDeviceToHost,
-                                ds);
-          if (e == cudaSuccess) e = cudaStreamSynchronize(ds);
-          if (e != cudaSuccess) ps = lp::report_cuda(e, "serving: deferred rows");
-        }
-        if (ps == LP_OK) {
-          for (int q = 0; q < nd; ++q) {
-            const size_t j = (size_t)D.h_dsrc[q];
-            std::memcpy(r->out.data() + j * k, D.h_dout.data() + (size_t)q * k,
-                        sizeof(lp_link) * k);
-            r->counts[j] = D.h_dcnt[q];
-          }
-          S->stats.deferred_sources += nd;
-        } else {
-          r->status = ps;
-          r->error = lp_last_error();
-        }
-      }
     } else {
       r->status = st == 2 ? LP_ECUDA : LP_EINTERNAL;
       r->error = st == 2 ? "the resident serving kernel failed" : "serving: device check failed";
     }
-    r->done = true;
+    if (r->deferred.empty()) {
+      r->done = true;
+      S->stats.completed += 1;
+    } else {
+      D.dq.push_back(r);  // done when the deferred rows are in
+      S->cv_work.notify_all();
+    }
     if (fin) {  // the slot and the pool room are free again
       D.pool.give(r->off, (long long)n);
       D.free_slots.push_back(r->slot);
@@ -486,7 +542,6 @@ void dev_harvest(lp_server* S) {
     }
     D.inflight[i] = D.inflight.back();
     D.inflight.pop_back();
-    S->stats.completed += 1;
     any = true;
   }
   while (!S->paused && st == 0 && !D.waiting.empty() && dev_admit(S, D.waiting.front()))
@@ -528,6 +583,7 @@ lp_status lp_serve_open(const lp_graph* g, const lp_serve_opts* opts, lp_server*
       delete S;
       return lp::report_cuda(e, "lp_serve_open");
     }
+    S->dev.dthread = std::thread(dev_deferred_main, S);
     *out = S;
     return LP_OK;
   }
@@ -693,17 +749,20 @@ lp_status lp_serve_close(lp_server* S) {
     S->closing = true;
     S->paused = false;
     DevLoop& D = S->dev;
-    for (;;) {  // finish every queued request
+    for (;;) {  // finish every queued request, deferred rows included
       dev_harvest(S);
-      if (D.inflight.empty() && D.waiting.empty()) break;
-      if (__atomic_load_n(D.status, __ATOMIC_ACQUIRE) != 0) {
-        dev_harvest(S);  // fails the rest
-        if (D.inflight.empty()) break;
-      }
+      bool all_done = true;
+      for (auto& kv : S->live) all_done = all_done && kv.second->done;
+      if (all_done || (D.inflight.empty() && D.dq.empty() &&
+                       __atomic_load_n(D.status, __ATOMIC_ACQUIRE) != 0))
+        break;
       S->cv_done.wait_for(lock, std::chrono::microseconds(50));
     }
     __atomic_store_n(D.stop, 1u, __ATOMIC_RELEASE);  // idle CTAs leave at once
+    D.dstop = true;
     lock.unlock();
+    S->cv_work.notify_all();
+    if (D.dthread.joinable()) D.dthread.join();
     dev_free(D);
     for (auto& kv : S->live) delete kv.second;
     S->live.clear();
