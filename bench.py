@@ -470,7 +470,7 @@ def run_serve(args):
                            "p99_ms": round(1e3 * float(np.percentile(lat_p, 99)), 2),
                            "edges_per_s": round(edges / span_p, 1)}}
         for mode in (0, 1):
-            entry["served" if mode == 0 else "served_host_batches"] = serve_once(
+            entry["served" if mode == 0 else "served_resident_kernel"] = serve_once(
                 lp, G, reqs, arr, plain_res, measure, k, cap, mode, args.slots, edges)
         out["loads"].append(entry)
     G.close()
@@ -479,8 +479,8 @@ def run_serve(args):
 
 def serve_once(lp, G, reqs, arr, plain_res, measure, k, cap, mode, slots, edges):
     """Submit every request at its arrival time to a server of the given mode
-    (0: resident kernel, 1: host batches), wait from several threads; latency
-    is completion minus arrival."""
+    (0: host batches, the default; 1: resident kernel), wait from several
+    threads; latency is completion minus arrival."""
     import threading
     R = len(reqs)
     S = lp.Server(G, slots=slots, max_batch_sources=65536, max_k=16, mode=mode)

@@ -344,11 +344,13 @@ typedef struct {
   int32_t max_k;             /* largest k accepted, <= LP_MAX_TOPK_PER_SOURCE (0: 16) */
   int32_t paused;            /* 1: queue requests but start no batch until
                                 lp_serve_resume                                   */
-  int32_t mode;              /* 0: a resident kernel serves the requests (below);
-                                1: host worker threads run batches               */
-  int32_t idle_polls;        /* mode 0: polls (about 4 us apart) a resident CTA
+  int32_t mode;              /* 0: host worker threads run batches (the default);
+                                1: a resident kernel serves the requests; it
+                                defers sources above defer_wedges to a host
+                                thread running the tiered pipeline             */
+  int32_t idle_polls;        /* mode 1: polls (about 4 us apart) a resident CTA
                                 waits for work before it leaves (0: 2500)        */
-  int32_t defer_wedges;      /* mode 0: a source with more wedges than this (its
+  int32_t defer_wedges;      /* mode 1: a source with more wedges than this (its
                                 hub-limited two-hop work) is not counted by the
                                 resident kernel but by the tiered per-source
                                 pipeline when its request is collected (0: 65536) */
@@ -359,12 +361,12 @@ typedef struct {
   int64_t completed;         /* requests finished (result ready or failed)        */
   int64_t batches;           /* device batches run                                */
   int64_t batched_sources;   /* sources over all batches                          */
-  int64_t max_batch_requests;/* most requests merged into one batch (mode 0: most
+  int64_t max_batch_requests;/* most requests merged into one batch (mode 1: most
                                 requests in flight on the device at once)        */
-  int64_t kernel_launches;   /* mode 0: launches of the resident kernel (it leaves
+  int64_t kernel_launches;   /* mode 1: launches of the resident kernel (it leaves
                                 after idle_polls polls without work and is
                                 launched again when work arrives)                */
-  int64_t deferred_sources;  /* mode 0: sources counted by the tiered pipeline
+  int64_t deferred_sources;  /* mode 1: sources counted by the tiered pipeline
                                 (more than defer_wedges wedges)                   */
 } lp_serve_stats;
 

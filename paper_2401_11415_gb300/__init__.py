@@ -462,8 +462,9 @@ class Batch:
 # ------------------------------------------------------------- serving --
 
 class Server:
-    """lp_serve_* wrapper: continuous batching of per-source queries (mode 0: a
-    resident kernel; mode 1: host worker threads running batches)."""
+    """lp_serve_* wrapper: continuous batching of per-source queries (mode 0:
+    host worker threads running batches, the default; mode 1: a resident
+    kernel)."""
 
     def __init__(self, graph, slots=0, max_batch_sources=0, max_pending=0, max_k=0,
                  paused=False, mode=0, idle_polls=0, defer_wedges=0):

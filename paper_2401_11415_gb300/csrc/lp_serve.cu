@@ -1,30 +1,33 @@
 // lp_serve.cu -- continuous batching of per-source queries (lp_serve_*).
 //
-// Mode 0 (the default): a resident kernel (lp_serve_dev.cu) serves the
-// requests.  An admitted request gets a request slot and room in two pools
-// of pinned host memory the GPU reads and writes directly: its sources and
-// its result rows.  The host writes them, one work item per source into a
-// ring, and then advances the ring's published count; the kernel's CTAs claim
-// the items and raise the slot's completion word after the last source.
-// Admission is by that memory: a request waits on the host until its sources
-// and rows (4 + 16 k bytes per source) fit in the pools, a slot is free and
-// the ring has room.  Finished requests are collected by any call that polls
-// (submit, wait, poll): their rows are copied out and their memory freed, so
-// waiting requests are admitted as memory frees up.  The kernel leaves when
-// it finds no work for idle_polls polls; a call that sees published work and
-// no kernel running launches it again.
+// Mode 0 (the default): requests (per-source top-k queries of uneven size)
+// are queued from any thread.  Each of `slots` workers owns a shadow view of
+// the graph (shared device arrays, its own stream and scratch) plus device
+// and pinned host buffers sized for max_batch_sources sources.  A worker
+// takes the oldest pending request and every other pending request with the
+// same (measure, hub limit, k) up to the source budget, runs them as one
+// per-source batch (lp_predict_sources semantics, the tiered kernels), and
+// scatters the rows back.  Requests that arrive while batches run are
+// admitted by the next free slot, so batches of different slots overlap on
+// the device.  Row i of a request depends only on its own source (the
+// per-source scan has no cross-source state), so a result is identical alone
+// and in any mix.
 //
-// Mode 1: requests (per-source top-k queries of uneven size) are queued from
-// any thread.  Each of `slots` workers owns a shadow view of the graph (shared
-// device arrays, its own stream and scratch) plus device and pinned host
-// buffers sized for max_batch_sources sources.  A worker takes the oldest
-// pending request and every other pending request with the same (measure,
-// hub limit, k) up to the source budget, runs them as one per-source batch
-// (lp_predict_sources semantics), and scatters the rows back.  Requests that
-// arrive while batches run are admitted by the next free slot, so batches of
-// different slots overlap on the device.  Row i of a request depends only on
-// its own source (the per-source scan has no cross-source state), so a result
-// is identical alone and in any mix.
+// Mode 1: a resident kernel (lp_serve_dev.cu) serves the requests.  An
+// admitted request gets a request slot and room in two pools of pinned host
+// memory the GPU reads and writes directly: its sources and its result rows.
+// The host writes them, one work item per source into a ring, and then
+// advances the ring's published count; the kernel's CTAs claim the items and
+// raise the slot's completion word after the last source.  Admission is by
+// that memory: a request waits on the host until its sources and rows
+// (4 + 16 k bytes per source) fit in the pools, a slot is free and the ring
+// has room.  Finished requests are collected by any call that polls (submit,
+// wait, poll): their rows are copied out and their memory freed, so waiting
+// requests are admitted as memory frees up.  The kernel leaves when it finds
+// no work for idle_polls polls; a call that sees published work and no kernel
+// running launches it again.  Sources with more than defer_wedges wedges are
+// left by the kernel to a host thread that runs them through the tiered
+// pipeline in batches.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -50,7 +53,7 @@ struct Request {
   lp_status status = LP_OK;
   std::string error;  // the worker's error text when status != LP_OK
   bool done = false;
-  // mode 0: where the admitted request lives
+  // mode 1: where the admitted request lives
   bool admitted = false;
   int slot = -1;
   long long off = 0;  // first source in the pools
@@ -92,7 +95,7 @@ struct RangeAlloc {
   }
 };
 
-// Mode 0 state: pools and ring in pinned host memory the GPU maps, claim and
+// Mode 1 state: pools and ring in pinned host memory the GPU maps, claim and
 // finish counters on the device.
 struct DevLoop {
   cudaStream_t stream = nullptr;  // the resident kernel's stream
@@ -246,7 +249,9 @@ void worker_main(lp_server* S, int si) {
 
 lp_status serve_fail(lp_status s, const char* msg) { return lp::report_error(s, msg); }
 
-// ------------------------------------------------------------ mode 0 ----
+// ------------------------------------------------------------ mode 1 ----
+
+constexpr int kResident = 1;  // lp_serve_opts.mode of the resident kernel
 
 int first_k(const std::vector<Request*>& batch) { return batch.empty() ? 1 : batch[0]->k; }
 
@@ -575,7 +580,7 @@ lp_status lp_serve_open(const lp_graph* g, const lp_serve_opts* opts, lp_server*
   S->base = &lp::graph_of(g);
   S->opts = o;
   S->paused = o.paused != 0;
-  if (o.mode == 0) {
+  if (o.mode == kResident) {
     cudaError_t e = cudaSetDevice(S->base->device);
     if (e == cudaSuccess) e = dev_open(S);
     if (e != cudaSuccess) {
@@ -630,7 +635,7 @@ lp_status lp_serve_submit(lp_server* S, const int32_t* sources, int32_t n_src, l
   r->cap = degree_cap < 0 ? -1 : degree_cap;
   r->k = k;
   r->sources.assign(sources, sources + n_src);
-  if (S->opts.mode == 0) {
+  if (S->opts.mode == kResident) {
     std::lock_guard<std::mutex> lock(S->mu);
     DevLoop& D = S->dev;
     if (S->closing) {
@@ -677,7 +682,7 @@ lp_status lp_serve_wait(lp_server* S, uint64_t req_id, int64_t timeout_us, lp_li
   auto it = S->live.find(req_id);
   if (it == S->live.end()) return serve_fail(LP_EINVAL, "lp_serve_wait: unknown request id");
   Request* r = it->second;
-  if (S->opts.mode == 0) {
+  if (S->opts.mode == kResident) {
     // poll: collect finished requests and keep the resident kernel running
     cudaSetDevice(S->base->device);
     const auto t0 = std::chrono::steady_clock::now();
@@ -712,7 +717,7 @@ lp_status lp_serve_resume(lp_server* S) {
   {
     std::lock_guard<std::mutex> lock(S->mu);
     S->paused = false;
-    if (S->opts.mode == 0) {
+    if (S->opts.mode == kResident) {
       cudaSetDevice(S->base->device);
       dev_harvest(S);
     }
@@ -726,7 +731,7 @@ lp_status lp_serve_poll(lp_server* S, uint64_t req_id, int32_t* done) {
   std::lock_guard<std::mutex> lock(S->mu);
   auto it = S->live.find(req_id);
   if (it == S->live.end()) return serve_fail(LP_EINVAL, "lp_serve_poll: unknown request id");
-  if (S->opts.mode == 0) {
+  if (S->opts.mode == kResident) {
     cudaSetDevice(S->base->device);
     dev_harvest(S);
   }
@@ -743,7 +748,7 @@ lp_status lp_serve_get_stats(lp_server* S, lp_serve_stats* out) {
 
 lp_status lp_serve_close(lp_server* S) {
   if (!S) return LP_OK;
-  if (S->opts.mode == 0) {
+  if (S->opts.mode == kResident) {
     std::unique_lock<std::mutex> lock(S->mu);
     cudaSetDevice(S->base->device);
     S->closing = true;

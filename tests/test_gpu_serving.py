@@ -1,8 +1,8 @@
 """lp_serve_*: continuous batching of per-source queries (needs a GPU).
 
-Mode 0 (the default) serves requests with a resident kernel that claims one
-source at a time from a ring in mapped host memory; mode 1 runs batches from
-host worker threads.  Both modes are checked the same way.
+Mode 0 (the default) runs batches from host worker threads; mode 1 serves
+requests with a resident kernel that claims one source at a time from a ring
+in mapped host memory.  Both modes are checked the same way.
 
 Each served result must equal lp_predict_sources on the same sources alone,
 whatever else is in the batch, and a quarter of the served requests (all four
@@ -140,7 +140,7 @@ def test_resident_kernel_leaves_when_idle_and_is_relaunched(lp, graph):
     g = graph
     rng = np.random.default_rng(3)
     with lp.Graph.from_csr(g) as G:
-        with lp.Server(G, slots=1, max_batch_sources=500, mode=0, idle_polls=20) as S:
+        with lp.Server(G, slots=1, max_batch_sources=500, mode=1, idle_polls=20) as S:
             for i in range(4):
                 src = rng.integers(0, g.n, 50 + 40 * i).astype(np.int32)
                 rid = S.submit(src, "RA", 10, 64)
@@ -161,7 +161,7 @@ def test_resident_kernel_admits_by_memory(lp, graph):
     rng = np.random.default_rng(4)
     reqs = [rng.integers(0, g.n, 40).astype(np.int32) for _ in range(12)]
     with lp.Graph.from_csr(g) as G:
-        with lp.Server(G, slots=1, max_batch_sources=64, max_k=8, mode=0) as S:
+        with lp.Server(G, slots=1, max_batch_sources=64, max_k=8, mode=1) as S:
             ids = [S.submit(r, "JC", 8, 64) for r in reqs]
             got = [S.wait(i, 60_000_000) for i in ids]
             st = S.stats()
@@ -180,7 +180,7 @@ def test_resident_kernel_defers_large_sources(lp, graph, measure, cap):
     rng = np.random.default_rng(9)
     reqs = [rng.integers(0, g.n, m).astype(np.int32) for m in (1, 17, 300, 900)]
     with lp.Graph.from_csr(g) as G:
-        with lp.Server(G, slots=2, max_batch_sources=1000, max_k=10, mode=0,
+        with lp.Server(G, slots=2, max_batch_sources=1000, max_k=10, mode=1,
                        defer_wedges=200) as S:
             ids = [S.submit(r, measure, 10, cap) for r in reqs]
             got = [S.wait(i, 60_000_000) for i in ids]
