@@ -925,9 +925,9 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
     if (measure == LP_AA || measure == LP_RA) {
       // grouped by the endpoint of larger degree: the top pairs share
       // high-degree endpoints, whose lists are then read once per group
-      CU(ensure(g, g.s_pair, pair_groups_scratch(g.n, nwrite)));
-      CU(launch_pair_cn_groups(d_links, nwrite, g.n, g.d_off, g.d_idx, g.d_arc, A.cap, g.s_pair.p,
-                               st, &t_stats.launches));
+      CU(ensure(g, g.s_pair, pair_groups_scratch(g.n, nwrite, A.cap < g.dmax ? g.arcs : 0)));
+      CU(launch_pair_cn_groups(d_links, nwrite, g.n, g.d_off, g.d_idx, g.d_deg, g.arcs, g.dmax,
+                               A.cap, g.s_pair.p, st, &t_stats.launches));
     }
     if (!out_dev)
       CU(cudaMemcpyAsync(out, d_links, sizeof(lp_link) * nwrite, cudaMemcpyDeviceToHost, st));
@@ -1002,9 +1002,9 @@ static lp_status merge_links(Graph& g, int measure, int cap, const lp_link* link
     CU(launch_emit_global(res, nwrite, measure, g.fixbits, d_links, st));
     t_stats.launches++;
     if (measure == LP_AA || measure == LP_RA) {
-      CU(ensure(g, g.s_pair, pair_groups_scratch(g.n, nwrite)));
-      CU(launch_pair_cn_groups(d_links, nwrite, g.n, g.d_off, g.d_idx, g.d_arc, A.cap, g.s_pair.p,
-                               st, &t_stats.launches));
+      CU(ensure(g, g.s_pair, pair_groups_scratch(g.n, nwrite, A.cap < g.dmax ? g.arcs : 0)));
+      CU(launch_pair_cn_groups(d_links, nwrite, g.n, g.d_off, g.d_idx, g.d_deg, g.arcs, g.dmax,
+                               A.cap, g.s_pair.p, st, &t_stats.launches));
     }
     CU(cudaMemcpyAsync(out, d_links, sizeof(lp_link) * nwrite, cudaMemcpyDeviceToHost, st));
   }

@@ -344,12 +344,13 @@ cudaError_t launch_emit_global(const Cand* c, u64 n, int measure, int fixbits, l
 cudaError_t launch_emit_sources(const TopEnt* top, const int* cnt, const int* sources, int n_src,
                                 int k, int measure, int fixbits, lp_link* out, cudaStream_t st);
 // Common-neighbour counts of global-mode links grouped by their endpoint of
-// larger degree (lp_pair.cu); pair_groups_scratch(n, links) bytes of device
-// scratch.
-size_t pair_groups_scratch(int n, u64 nlinks);
+// larger degree (lp_pair.cu); pair_groups_scratch(n, links, kept_arcs) bytes
+// of device scratch, kept_arcs = the arc count when cap < dmax (the kept
+// lists are built), else 0.
+size_t pair_groups_scratch(int n, u64 nlinks, long long kept_arcs);
 cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off, const int* idx,
-                                  const Arc* arc, int cap, void* scratch, cudaStream_t st,
-                                  int* launches);
+                                  const int* deg, long long arcs, int dmax, int cap, void* scratch,
+                                  cudaStream_t st, int* launches);
 cudaError_t launch_pair_cn(lp_link* links, const int* cnt_rows, int k, u64 n, const int* off,
                            const int* idx, const int* deg, const Arc* arc, int cap,
                            cudaStream_t st);

@@ -5,12 +5,18 @@
 // every predicted link reports (Section 4.1.5) is recomputed for the links the
 // selection kept.  Their top pairs join high-degree vertices, and a vertex
 // takes part in many of them, so the links are grouped by their endpoint of
-// larger degree, u: one CTA marks Gamma_u (hub test applied) in shared memory
+// larger degree, u.  A small group (short Gamma_u, few links) is one warp's:
+// a hash set of Gamma_u in the warp's slice of shared memory, then each link
+// (u, v) counts the entries of Gamma_v found in it.  For the others one CTA
+// marks Gamma_u (hub test applied) in shared memory
 // (a bitmap over the vertex ids, in windows of ids when they do not all fit,
 // or a hash set when Gamma_u is short and the ids need several windows), and
 // its warps count, for every link (u, v) of the group, the marked entries of
 // the shorter Gamma_v.  Building the groups is a counting sort by u
-// (histogram, scan, scatter) in a handful of small kernels.
+// (histogram, scan, scatter) in a handful of small kernels.  Under a hub
+// limit both sides read a kept copy of the lists (the entries b with
+// |Gamma_b| <= L_H, in order), built per call: a hub's list keeps about a
+// third of its entries on the power-law graphs, and the walks shrink with it.
 #include "lp_internal.cuh"
 
 namespace lp {
@@ -20,8 +26,8 @@ namespace lp {
 constexpr int kScanThreads = 1024;
 constexpr int kScanChunk = kScanThreads * 4;  // int2 entries per block
 
-// A link is grouped under its endpoint of larger degree (u on a tie), so
-// the list streamed per link is the shorter one.
+// A link is grouped under its endpoint with the longer (kept) list (u on a
+// tie), so the list streamed per link is the shorter one.
 __device__ __forceinline__ int pair_owner(const lp_link& L, const int* __restrict__ off) {
   const int du = off[L.u + 1] - off[L.u], dv = off[L.v + 1] - off[L.v];
   return du >= dv ? L.u : L.v;
@@ -132,12 +138,147 @@ __global__ void k_scan_add(int2* __restrict__ sc, int n, const int2* __restrict_
   }
 }
 
-// groups[g] = (u, first position in perm, links of u); cnt: the histogram
-// (kept apart from the scanned array sc).
-__global__ void k_pair_groups(const int* __restrict__ cnt, const int2* __restrict__ sc, int n,
-                              int4* __restrict__ groups) {
+// Kept lists under a hub limit: kcnt[v] = |{b in Gamma_v : |Gamma_b| <= cap}|
+// (a warp per vertex), and after the scan of kcnt into koff the entries
+// themselves, in their order in Gamma_v.
+__global__ void k_kept_count(const int* __restrict__ off, const int* __restrict__ idx,
+                             const int* __restrict__ deg, int n, int cap, int* __restrict__ kcnt) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nwarps) {
+    const int e0 = off[v], e1 = off[v + 1];
+    int c = 0;
+    for (int e = e0 + lane; e < e1; e += 32) c += __ldg(deg + __ldg(idx + e)) <= cap ? 1 : 0;
+    c = (int)__reduce_add_sync(FULLMASK, (u32)c);
+    if (lane == 0) kcnt[v] = c;
+  }
+}
+
+__global__ void k_kept_scatter(const int* __restrict__ off, const int* __restrict__ idx,
+                               const int* __restrict__ deg, int n, int cap,
+                               const int2* __restrict__ koff, int* __restrict__ kidx) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nwarps) {
+    const int e0 = off[v], e1 = off[v + 1];
+    int o = koff[v].x;
+    for (int eb = e0; eb < e1; eb += 32) {  // warp-uniform trips
+      const int e = eb + lane;
+      const int b = e < e1 ? __ldg(idx + e) : 0;
+      const bool keep = e < e1 && __ldg(deg + b) <= cap;
+      const u32 m = __ballot_sync(FULLMASK, keep);
+      if (keep) kidx[o + __popc(m & ((1u << lane) - 1u))] = b;
+      o += __popc(m);
+    }
+  }
+}
+
+// koff[i] = koff2[i].x for i <= n (the scan leaves (prefix, flags) pairs).
+__global__ void k_kept_offsets(const int2* __restrict__ koff2, int n1, int* __restrict__ koff) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n1) koff[i] = koff2[i].x;
+}
+
+// A group whose owner list has at most kSmallDeg entries and which has at
+// most kSmallLinks links is counted by one warp with a hash set of its own
+// (kSmallLog slots: at most a quarter taken); the others by a whole CTA.
+constexpr int kSmallDeg = 256;
+constexpr int kSmallLinks = 64;
+constexpr int kSmallLog = 10;
+constexpr int kSmallWarps = 8;  // per 256-thread CTA: 32 KB of tables
+
+// groups[g] = (u, first position in perm, links of u), warp groups from the
+// front (count nsg[0]), CTA groups from the back (count nsg[1]); cnt: the
+// histogram (kept apart from the scanned array sc).
+__global__ void k_pair_groups(const int* __restrict__ cnt, const int2* __restrict__ sc,
+                              const int* __restrict__ off, int n, int4* __restrict__ groups,
+                              u32* __restrict__ nsg) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u < n && cnt[u] > 0) groups[sc[u].y] = make_int4(u, sc[u].x, cnt[u], 0);
+  if (u < n && cnt[u] > 0) {
+    const int4 G = make_int4(u, sc[u].x, cnt[u], 0);
+    if (off[u + 1] - off[u] <= kSmallDeg && cnt[u] <= kSmallLinks)
+      groups[atomicAdd(&nsg[0], 1u)] = G;
+    else
+      groups[n - 1 - (int)atomicAdd(&nsg[1], 1u)] = G;
+  }
+}
+
+__device__ __forceinline__ u32 small_hash(int b) {
+  return ((u32)b * 0x9E3779B1u) >> (32 - kSmallLog);
+}
+
+// 1 if b is in the warp's set (keys b + 1, 0 = empty; an empty slot always
+// comes, as at most a quarter are taken).
+__device__ __forceinline__ u32 small_has(const u32* t, int b) {
+  const u32 key = (u32)b + 1u;
+  u32 h = small_hash(b);
+  for (;;) {
+    const u32 k2 = t[h];
+    if (k2 == key) return 1u;
+    if (k2 == 0u) return 0u;
+    h = (h + 1) & ((1u << kSmallLog) - 1);
+  }
+}
+
+// The warp groups: a warp claims a group, puts the owner's list in its set,
+// counts every link's other list against it (four loads in flight per lane)
+// and clears the slots it took.
+__global__ void __launch_bounds__(kSmallWarps * 32) k_pair_cn_small(lp_link* __restrict__ links,
+                                                                   const int* __restrict__ perm,
+                                                                   const int4* __restrict__ groups,
+                                                                   const u32* __restrict__ nsg,
+                                                                   const int* __restrict__ off,
+                                                                   const int* __restrict__ idx,
+                                                                   u32* __restrict__ claim) {
+  __shared__ u32 tab[kSmallWarps][1 << kSmallLog];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  u32* t = tab[wid];
+  for (int i = lane; i < (1 << kSmallLog); i += 32) t[i] = 0;
+  __syncwarp();
+  const u32 ng = nsg[0];
+  for (;;) {
+    u32 gi = 0;
+    if (lane == 0) gi = atomicAdd(claim, 1u);
+    gi = __shfl_sync(FULLMASK, gi, 0);
+    if (gi >= ng) break;
+    const int4 G = groups[gi];
+    const int u = G.x, e0 = off[u], e1 = off[u + 1];
+    int slot[kSmallDeg / 32];
+#pragma unroll
+    for (int q = 0; q < kSmallDeg / 32; ++q) {
+      slot[q] = -1;
+      const int e = e0 + q * 32 + lane;
+      if (e < e1) {
+        const int b = __ldg(idx + e);
+        u32 h = small_hash(b);
+        while (atomicCAS(&t[h], 0u, (u32)b + 1u) != 0u)  // keys are distinct
+          h = (h + 1) & ((1u << kSmallLog) - 1);
+        slot[q] = (int)h;
+      }
+    }
+    __syncwarp();
+    for (int j = 0; j < G.z; ++j) {
+      const int li = perm[G.y + j];
+      const int lu = links[li].u, lv = links[li].v;
+      const int v = lu == u ? lv : lu;
+      const int vs = off[v], ve = off[v + 1];
+      u32 c = 0;
+      int e = vs + lane;
+      for (; e + 96 < ve; e += 128) {
+        const int b0 = __ldg(idx + e), b1 = __ldg(idx + e + 32), b2 = __ldg(idx + e + 64),
+                  b3 = __ldg(idx + e + 96);
+        c += small_has(t, b0) + small_has(t, b1) + small_has(t, b2) + small_has(t, b3);
+      }
+      for (; e < ve; e += 32) c += small_has(t, __ldg(idx + e));
+      c = __reduce_add_sync(FULLMASK, c);
+      if (lane == 0) links[li].cn = (int)c;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < kSmallDeg / 32; ++q)
+      if (slot[q] >= 0) t[slot[q]] = 0u;
+    __syncwarp();
+  }
 }
 
 // perm: link indices grouped by u (the group starts in sc[u].x serve as
@@ -156,27 +297,27 @@ __device__ __forceinline__ u32 pair_hash(int b) {
   return ((u32)b * 0x9E3779B1u) >> (32 - kPairHashLog);
 }
 
-// One group at a time per CTA (claimed from *claim): the marked set is Gamma_u
-// (b with |Gamma_b| <= cap); every link (u, v) of the group counts the marked
-// entries of Gamma_v (a warp per link).  The set is a bitmap over the ids
+// One group at a time per CTA (claimed from *claim): the marked set is the
+// kept list of u (off / idx: the kept lists, or the whole lists without a hub
+// limit); every link (u, v) of the group counts the marked entries of v's
+// list (a warp per link).  The set is a bitmap over the ids
 // [w0, w0 + 32 * nwords): over all vertices when they fit, else one window of
 // ids at a time; a group whose Gamma_u is short uses a hash set of its
 // entries (keys b + 1, 0 = empty) in the same shared memory instead.
-// *ngroups is the total the scan left after the last vertex.
+// Its groups are the CTA groups, counted from the back of groups (nsg[1]).
 __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict__ links,
                                                             const int* __restrict__ perm,
                                                             const int4* __restrict__ groups,
-                                                            const int2* __restrict__ total,
+                                                            const u32* __restrict__ nsg,
                                                             const int* __restrict__ off,
                                                             const int* __restrict__ idx,
-                                                            const Arc* __restrict__ arc, int cap,
                                                             int nwords, int n,
                                                             u32* __restrict__ claim,
                                                             int* __restrict__ cur) {
   extern __shared__ u32 bits[];
   __shared__ u32 s_g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const u32 ngroups = (u32)total->y;
+  const u32 ngroups = nsg[1];
   const int width = nwords * 32;
   const bool one_window = n <= width;
   for (int i = threadIdx.x; i < nwords; i += blockDim.x) bits[i] = 0;
@@ -185,14 +326,13 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
     __syncthreads();
     const u32 gi = s_g;
     if (gi >= ngroups) break;
-    const int4 G = groups[gi];
+    const int4 G = groups[n - 1 - (int)gi];
     const int u = G.x, e0 = off[u], e1 = off[u + 1];
     if (!one_window && e1 - e0 <= kPairHashMaxDeg) {
       for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const Arc t = arc[e];  // b = t.w, |Gamma_b| = t.z
-        if (t.z > cap) continue;
-        u32 h = pair_hash(t.w);
-        while (atomicCAS(&bits[h], 0u, (u32)t.w + 1u) != 0u)  // keys are distinct
+        const int b = __ldg(idx + e);
+        u32 h = pair_hash(b);
+        while (atomicCAS(&bits[h], 0u, (u32)b + 1u) != 0u)  // keys are distinct
           h = (h + 1) & ((1u << kPairHashLog) - 1);
       }
       __syncthreads();
@@ -200,18 +340,27 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
         const int li = perm[G.y + j];
         const lp_link L = links[li];
         const int v = L.u == u ? L.v : L.u;
-        int c = 0;
-        for (int e = off[v] + lane; e < off[v + 1]; e += 32) {
-          const u32 key = (u32)__ldg(idx + e) + 1u;
-          u32 h = pair_hash((int)key - 1);
-          for (;;) {  // at most half the slots are taken, so an empty one comes
+        // at most half the slots are taken, so an empty one comes
+        auto has = [&](int b) -> u32 {
+          const u32 key = (u32)b + 1u;
+          u32 h = pair_hash(b);
+          for (;;) {
             const u32 k2 = bits[h];
-            if (k2 == key) { ++c; break; }
-            if (k2 == 0u) break;
+            if (k2 == key) return 1u;
+            if (k2 == 0u) return 0u;
             h = (h + 1) & ((1u << kPairHashLog) - 1);
           }
+        };
+        u32 c = 0;
+        const int ve = off[v + 1];
+        int e = off[v] + lane;
+        for (; e + 96 < ve; e += 128) {  // four loads in flight per lane
+          const int b0 = __ldg(idx + e), b1 = __ldg(idx + e + 32), b2 = __ldg(idx + e + 64),
+                    b3 = __ldg(idx + e + 96);
+          c += has(b0) + has(b1) + has(b2) + has(b3);
         }
-        c = __reduce_add_sync(FULLMASK, (u32)c);
+        for (; e < ve; e += 32) c += has(__ldg(idx + e));
+        c = __reduce_add_sync(FULLMASK, c);
         if (lane == 0) links[li].cn = c;
       }
       __syncthreads();
@@ -224,7 +373,7 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
       for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const int b = __ldg(idx + e);
         if (b < w0 || b >= w1) continue;
-        if (arc[e].z <= cap) atomicOr(&bits[(b - w0) >> 5], 1u << ((b - w0) & 31));
+        atomicOr(&bits[(b - w0) >> 5], 1u << ((b - w0) & 31));
       }
       __syncthreads();
       for (int j = wid; j < G.z; j += nw) {  // warp-uniform trips
@@ -295,24 +444,28 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
 }
 
 // Scratch layout: sc int2[n + 1], cnt int[n + 1], perm int[links], groups
-// int4[n], sums int2[chunks], claim u32, window cursors int[links]; every
+// int4[n], sums int2[chunks], claim u32, window cursors int[links]; under a
+// hub limit also the kept lists: koff int[n + 1] and kidx int[arcs]; every
 // part 256-byte aligned (groups are written as int4).
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-size_t pair_groups_scratch(int n, u64 nlinks) {
+size_t pair_groups_scratch(int n, u64 nlinks, long long kept_arcs) {
   const size_t n1 = (size_t)n + 1;
-  return align256(n1 * sizeof(int2)) + align256(n1 * sizeof(int)) + align256(nlinks * sizeof(int)) +
-         align256((size_t)n * sizeof(int4)) +
-         align256(((n1 + kScanChunk - 1) / kScanChunk) * sizeof(int2)) + 256 +
-         align256(nlinks * sizeof(int));
+  size_t b = align256(n1 * sizeof(int2)) + align256(n1 * sizeof(int)) +
+             align256(nlinks * sizeof(int)) + align256((size_t)n * sizeof(int4)) +
+             align256(((n1 + kScanChunk - 1) / kScanChunk) * sizeof(int2)) + 256 +
+             align256(nlinks * sizeof(int));
+  if (kept_arcs > 0) b += align256(n1 * sizeof(int)) + align256((size_t)kept_arcs * sizeof(int));
+  return b;
 }
 
 // Counts of links[0, n), grouped by the endpoint of larger degree; scratch of pair_groups_scratch bytes.
 cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off, const int* idx,
-                                  const Arc* arc, int cap, void* scratch, cudaStream_t st,
-                                  int* launches) {
+                                  const int* deg, long long arcs, int dmax, int cap, void* scratch,
+                                  cudaStream_t st, int* launches) {
   if (n == 0) return cudaSuccess;
   const int n1 = nv + 1;
+  const bool kept = cap < dmax;  // else every list is kept whole
   char* p = static_cast<char*>(scratch);
   int2* sc = reinterpret_cast<int2*>(p);
   p += align256((size_t)n1 * sizeof(int2));
@@ -328,15 +481,42 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
   u32* claim = reinterpret_cast<u32*>(p);
   p += 256;
   int* cur = reinterpret_cast<int*>(p);
-  cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)n1 * sizeof(int), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(claim, 0, sizeof(u32), st);
+  p += align256(n * sizeof(int));
+  int dev = 0, nsm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaSuccess;
+  if (kept) {
+    // the kept lists: counts (in cnt), their scan (in sc, as the groups'
+    // scan below does), offsets, entries; sc and cnt are reset afterwards
+    int* koff = reinterpret_cast<int*>(p);
+    p += align256((size_t)n1 * sizeof(int));
+    int* kidx = reinterpret_cast<int*>(p);
+    const int wb = nsm * 8;  // 256-thread blocks, a warp per vertex
+    k_kept_count<<<wb, 256, 0, st>>>(off, idx, deg, nv, cap, cnt);
+    e = cudaMemsetAsync(cnt + nv, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_scan_counts<<<nb, kScanThreads, 0, st>>>(cnt, n1, sc, sums);
+    k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, nb);
+    k_scan_add<<<(n1 + 255) / 256, 256, 0, st>>>(sc, n1, sums);
+    k_kept_offsets<<<(n1 + 255) / 256, 256, 0, st>>>(sc, n1, koff);
+    k_kept_scatter<<<wb, 256, 0, st>>>(off, idx, deg, nv, cap, sc, kidx);
+    if (launches) *launches += 6;
+    off = koff;
+    idx = kidx;
+  }
+  (void)arcs;
+  e = cudaMemsetAsync(cnt, 0, (size_t)n1 * sizeof(int), st);
+  // claim: [0] CTA groups claimed, [1] warp groups claimed, [2] / [3] warp /
+  // CTA groups written
+  if (e == cudaSuccess) e = cudaMemsetAsync(claim, 0, 4 * sizeof(u32), st);
   if (e != cudaSuccess) return e;
   const int gb = (int)std::min<u64>((n + 255) / 256, 152 * 8);
   k_pair_hist<<<gb, 256, 0, st>>>(links, n, off, cnt);
   k_scan_counts<<<nb, kScanThreads, 0, st>>>(cnt, n1, sc, sums);
   k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, nb);
   k_scan_add<<<(n1 + 255) / 256, 256, 0, st>>>(sc, n1, sums);
-  k_pair_groups<<<(nv + 255) / 256, 256, 0, st>>>(cnt, sc, nv, groups);
+  k_pair_groups<<<(nv + 255) / 256, 256, 0, st>>>(cnt, sc, off, nv, groups, claim + 2);
   k_pair_scatter<<<gb, 256, 0, st>>>(links, n, off, sc, perm);
   // a bitmap over every vertex when it fits in 224 KB, else windows of that
   // size (and room for the hash set)
@@ -345,12 +525,11 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
   e = cudaFuncSetAttribute(k_pair_cn_groups, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            224 * 1024);
   if (e != cudaSuccess) return e;
-  int dev = 0, nsm = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  k_pair_cn_groups<<<nsm, 1024, smem, st>>>(links, perm, groups, sc + nv, off, idx, arc, cap,
-                                            nwords, nv, claim, cur);
-  if (launches) *launches += 7;
+  k_pair_cn_small<<<nsm * 7, kSmallWarps * 32, 0, st>>>(links, perm, groups, claim + 2, off, idx,
+                                                        claim + 1);
+  k_pair_cn_groups<<<nsm, 1024, smem, st>>>(links, perm, groups, claim + 2, off, idx, nwords, nv,
+                                            claim, cur);
+  if (launches) *launches += 8;
   return cudaGetLastError();
 }
 

@@ -961,38 +961,60 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
         }
         __syncthreads();
         const int npieces = npl + (tsw + kPiece - 1) / kPiece;
-        for (int p = wid; p < npieces; p += NW) {  // warp-uniform trips
-          int c8[kPerLane], j8[kPerLane];
+        // A warp takes pieces p = wid, wid + NW, ...: the loads of its next
+        // piece are issued before the inserts of the current one.
+        int jl = 0;   // long segment of the warp's last piece
+        int jsh = H;  // short segment of the lane's last wedge
+        auto fetch = [&](int p, int (&c8)[kPerLane], int (&j8)[kPerLane]) {
           if (p < npl) {
-            const int j = last_le(c_p, 0, nl, p);
-            const int off = (p - c_p[j]) * kPiece;
-            const int plen = min(kPiece, c_l[j] - off);
-            const int* src = A.idx + c_s[j] + off;
+            // c_p rises strictly over the long segments and the last piece,
+            // p - NW, lay in segment jl: p lies in one of jl .. jl + NW, and
+            // one ballot over the next 32 starts finds it
+            const int cand = jl + 1 + lane;
+            jl += __popc(__ballot_sync(FULLMASK, cand < nl && c_p[cand] <= p));
+            const int off = (p - c_p[jl]) * kPiece;
+            const int plen = min(kPiece, c_l[jl] - off);
+            const int* src = A.idx + c_s[jl] + off;
 #pragma unroll
             for (int u = 0; u < kPerLane; ++u) {
               c8[u] = lane + 32 * u < plen ? __ldg(src + lane + 32 * u) : -1;
-              j8[u] = j;
+              j8[u] = jl;
             }
           } else {
             const int i0 = (p - npl) * kPiece + lane;
-            int jj = i0 < tsw ? last_le(c_p, H, H + ns, i0) : H;
+            // the lane's wedges rise from piece to piece
+            if (i0 < tsw) jsh = last_le(c_p, jsh, H + ns, i0);
 #pragma unroll
             for (int u = 0; u < kPerLane; ++u) {
               const int i = i0 + 32 * u;
               c8[u] = -1;
               if (i < tsw) {
-                // i - 32 lay in segment jj and segments are not empty, so i
-                // lies in one of the segments jj .. jj + 32
-                if (jj + 1 < H + ns && c_p[jj + 1] <= i) jj = last_le(c_p, jj + 1, min(H + ns, jj + 33), i);
-                c8[u] = __ldg(A.idx + c_s[jj] + i);
+                // i - 32 lay in segment jsh and segments are not empty, so i
+                // lies in one of the segments jsh .. jsh + 32
+                if (jsh + 1 < H + ns && c_p[jsh + 1] <= i)
+                  jsh = last_le(c_p, jsh + 1, min(H + ns, jsh + 33), i);
+                c8[u] = __ldg(A.idx + c_s[jsh] + i);
               }
-              j8[u] = jj;
+              j8[u] = jsh;
             }
           }
+        };
+        int c8[kPerLane], j8[kPerLane];
+        if (wid < npieces) fetch(wid, c8, j8);
+        for (int p = wid; p < npieces; p += NW) {  // warp-uniform trips
+          int n8[kPerLane], m8[kPerLane];
+#pragma unroll
+          for (int u = 0; u < kPerLane; ++u) n8[u] = m8[u] = -1;
+          if (p + NW < npieces) fetch(p + NW, n8, m8);
 #pragma unroll
           for (int u = 0; u < kPerLane; ++u)
             if (c8[u] >= 0) insert(c8[u], V64 ? (V)c_w[j8[u]] : (V)1);
           if (!is_dense && __any_sync(FULLMASK, *(volatile int*)&s_overflow != 0)) break;
+#pragma unroll
+          for (int u = 0; u < kPerLane; ++u) {
+            c8[u] = n8[u];
+            j8[u] = m8[u];
+          }
         }
         __syncthreads();
       }
