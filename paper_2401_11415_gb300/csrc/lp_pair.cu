@@ -311,23 +311,107 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
                                                             const u32* __restrict__ nsg,
                                                             const int* __restrict__ off,
                                                             const int* __restrict__ idx,
+                                                            const int* __restrict__ foff,
+                                                            const int* __restrict__ fidx,
+                                                            const int* __restrict__ deg,
                                                             int nwords, int n,
                                                             u32* __restrict__ claim,
                                                             int* __restrict__ cur) {
   extern __shared__ u32 bits[];
   __shared__ u32 s_g;
+  __shared__ unsigned long long s_cost[2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const u32 ngroups = nsg[1];
   const int width = nwords * 32;
   const bool one_window = n <= width;
+  // the table of the wedge form: slots keys then slots counts, half the slots
+  // taken at most (a chunk of the group's links at a time)
+  const int slog = 31 - __clz(nwords / 2);
+  const int slots = 1 << slog, chunk = slots / 2;
+  u32* tkey = bits;
+  u32* tcnt = bits + slots;
   for (int i = threadIdx.x; i < nwords; i += blockDim.x) bits[i] = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_g = atomicAdd(claim, 1u);
+    if (threadIdx.x == 0) {
+      s_g = atomicAdd(claim, 1u);
+      s_cost[0] = s_cost[1] = 0ull;
+    }
     __syncthreads();
     const u32 gi = s_g;
     if (gi >= ngroups) break;
     const int4 G = groups[n - 1 - (int)gi];
     const int u = G.x, e0 = off[u], e1 = off[u + 1];
+    // Two ways to count: walk every link's list (the sum of their lengths),
+    // or expand the wedges of u once per chunk of links (the kept b of u,
+    // each with its whole list Gamma_b) and look every second-order vertex up
+    // in a table of the chunk's other endpoints.  The cheaper one is taken.
+    {
+      unsigned long long wk = 0, wg = 0;
+      for (int j = threadIdx.x; j < G.z; j += blockDim.x) {
+        const int li = perm[G.y + j];
+        const int lu = links[li].u, lv = links[li].v;
+        const int v = lu == u ? lv : lu;
+        wk += (unsigned long long)(off[v + 1] - off[v]);
+      }
+      for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x)
+        wg += (unsigned long long)__ldg(deg + __ldg(idx + e));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        wk += __shfl_xor_sync(FULLMASK, wk, o);
+        wg += __shfl_xor_sync(FULLMASK, wg, o);
+      }
+      if (lane == 0) {
+        atomicAdd(&s_cost[0], wk);
+        atomicAdd(&s_cost[1], wg);
+      }
+    }
+    __syncthreads();
+    const unsigned long long nchunks = ((unsigned long long)G.z + chunk - 1) / chunk;
+    if (s_cost[1] * nchunks < s_cost[0]) {  // CTA-uniform
+      for (int c0 = 0; c0 < G.z; c0 += chunk) {
+        const int c1 = min(G.z, c0 + chunk);
+        for (int j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+          const int li = perm[G.y + j];
+          const int lu = links[li].u, lv = links[li].v;
+          const int v = lu == u ? lv : lu;
+          u32 h = ((u32)v * 0x9E3779B1u) >> (32 - slog);
+          while (atomicCAS(&tkey[h], 0u, (u32)v + 1u) != 0u)  // the endpoints are distinct
+            h = (h + 1) & (slots - 1);
+        }
+        __syncthreads();
+        for (int e = e0 + wid; e < e1; e += nw) {  // a warp per kept b of u
+          const int b = __ldg(idx + e);
+          const int fe = __ldg(foff + b + 1);
+          for (int f = __ldg(foff + b) + lane; f < fe; f += 32) {
+            const int c = __ldg(fidx + f);
+            const u32 key = (u32)c + 1u;
+            u32 h = ((u32)c * 0x9E3779B1u) >> (32 - slog);
+            for (;;) {  // at most half the slots are taken, so an empty one comes
+              const u32 k2 = tkey[h];
+              if (k2 == key) {
+                atomicAdd(&tcnt[h], 1u);
+                break;
+              }
+              if (k2 == 0u) break;
+              h = (h + 1) & (slots - 1);
+            }
+          }
+        }
+        __syncthreads();
+        for (int j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+          const int li = perm[G.y + j];
+          const int lu = links[li].u, lv = links[li].v;
+          const int v = lu == u ? lv : lu;
+          u32 h = ((u32)v * 0x9E3779B1u) >> (32 - slog);
+          while (tkey[h] != (u32)v + 1u) h = (h + 1) & (slots - 1);  // it is there
+          links[li].cn = (int)tcnt[h];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 2 * slots; i += blockDim.x) bits[i] = 0;
+        __syncthreads();
+      }
+      continue;
+    }
     if (!one_window && e1 - e0 <= kPairHashMaxDeg) {
       for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const int b = __ldg(idx + e);
@@ -466,6 +550,8 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
   if (n == 0) return cudaSuccess;
   const int n1 = nv + 1;
   const bool kept = cap < dmax;  // else every list is kept whole
+  const int* foff = off;  // the whole lists (second-order vertices of the wedge form)
+  const int* fidx = idx;
   char* p = static_cast<char*>(scratch);
   int2* sc = reinterpret_cast<int2*>(p);
   p += align256((size_t)n1 * sizeof(int2));
@@ -527,8 +613,8 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
   if (e != cudaSuccess) return e;
   k_pair_cn_small<<<nsm * 7, kSmallWarps * 32, 0, st>>>(links, perm, groups, claim + 2, off, idx,
                                                         claim + 1);
-  k_pair_cn_groups<<<nsm, 1024, smem, st>>>(links, perm, groups, claim + 2, off, idx, nwords, nv,
-                                            claim, cur);
+  k_pair_cn_groups<<<nsm, 1024, smem, st>>>(links, perm, groups, claim + 2, off, idx, foff, fidx,
+                                            deg, nwords, nv, claim, cur);
   if (launches) *launches += 8;
   return cudaGetLastError();
 }

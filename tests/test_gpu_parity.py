@@ -97,6 +97,17 @@ def test_all_candidates_and_threshold(lp):
             check_global(lp, g, m, 16, 25, th)
 
 
+def test_pair_counts_large_groups(lp):
+    # AA / RA report |Gamma_u ∩ Gamma_v| (kept intermediaries) for every link;
+    # with many links per endpoint the counts come from the CTA forms (bitmap
+    # walk or the endpoint's wedges against a table of its links), with few
+    # from the warp form, and under a hub limit from the kept lists
+    g = L.chung_lu(3000, 12.0, 2.05, dmax=1500, seed=21)
+    for m in ("AA", "RA"):
+        for cap in (None, 64, 16):
+            check_global(lp, g, m, cap, 150000)
+
+
 def test_degenerate_graphs(lp):
     empty = L.Graph(0, np.zeros(1, np.int32), np.zeros(0, np.int32))
     assert len(run_global(lp, empty, "JC", None, 10)) == 0
