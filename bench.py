@@ -18,10 +18,10 @@ roofline: the dominant scan kernel, algorithmic bytes (Gamma_a ids, degree of
        event-timed duration.
 the benchmark spec: the same measurements for R-MAT scale 24 (16,777,216 vertices,
        10% held out), DLH hub limit 256, JC and RA, N_P = |E^U|.
-cpu_baseline: the CPU oracle, run once outside the timed region, on all host
-       cores and on one thread: by default over a bounded sample of the step
-       (its DLH cap-16 JC and RA calls, about 10 s); --cpu-baseline full times
-       all ten calls (about 4 minutes on 16 cores).
+cpu_baseline: the CPU oracle on all host cores over the ten calls of the
+       step, run once outside the timed region (about 4 minutes on 16 cores;
+       --cpu-baseline sample times only the cap-16 pair), plus the cap-16 pair
+       on one thread.
 
 --impl reference runs the CPU oracle (the only reference this method has)
 on a bounded sample of the same workload (the cap-16 JC and RA calls per
@@ -378,7 +378,7 @@ def run_e2e(lp, torch, obs, k, steps):
             "d2h_bytes_per_step": int(16 * total / steps)}
 
 
-def cpu_baseline(split, which="sample"):
+def cpu_baseline(split, which="full"):
     """The oracle on all host cores, once: over the ten calls of the step
     ("full", the same work as the timed step) or the cap-16 pair ("sample");
     and the cap-16 pair on one thread."""
@@ -692,7 +692,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-baseline", default="sample", choices=["full", "sample"],
+    ap.add_argument("--cpu-baseline", default="full", choices=["full", "sample"],
                     help="oracle over all ten calls (full) or the cap-16 pair (sample)")
     ap.add_argument("--no-north-star", action="store_true",
                     help="skip the R-MAT scale-24 DLH(256) record")
