@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
   __shared__ int4 s_rec, s_rec_next;
   __shared__ ExpUnit s_unit, s_unit_next;
   __shared__ u64 s_next;
-  __shared__ int s_ndistinct, s_overflow, s_fail, s_e0, s_e1;
+  __shared__ int s_overflow, s_fail, s_e0, s_e1;
   const int lane = lane_id(), wid = threadIdx.x >> 5;
   for (int i = threadIdx.x * 16; i < kExpTableBytes; i += kCountThreads * 16)
     *reinterpret_cast<int4*>(smem + i) = make_int4(0, 0, 0, 0);
@@ -307,7 +307,6 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
       s_rec = s_rec_next;
       s_unit = s_unit_next;
       s_fail = 0;
-      s_ndistinct = 0;
       s_overflow = 0;
     }
     __syncthreads();
@@ -369,8 +368,8 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
       s_next = *(volatile u32*)&A.ctr->full ? ~0ull : atomicAdd(claim, 1ull);
       fetch(s_next, s_rec_next, s_unit_next);
     }
-    // a table that receives at most `limit` records cannot fill: then no
-    // distinct-key count and no overflow test is needed
+    // a table that receives at most `limit` records stays at most three
+    // quarters full: then it is probed to the end and never overflows
     const int R = s_pre[nt];
     const bool guard = !dense && R > limit;
     auto insert = [&](int c, V wc) {
@@ -392,12 +391,7 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
         hash_add<V>(keys, vals, logcap, c, wc);
       } else {
         if (*(volatile int*)&s_overflow) return;
-        const int rc = hash_add<V>(keys, vals, logcap, c, wc);
-        if (rc == 1) {
-          if (atomicAdd(&s_ndistinct, 1) >= limit) s_overflow = 1;
-        } else if (rc == 2) {
-          s_overflow = 1;
-        }
+        if (hash_add<V>(keys, vals, logcap, c, wc, fill_probes(logcap)) == 2) s_overflow = 1;
       }
     };
     // insert the bucket's records: warp w > 0 takes the flattened records

@@ -466,7 +466,6 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 8)) k_scan_cta(
   TopEnt* tops = reinterpret_cast<TopEnt*>(smem + table_bytes);
   __shared__ int4 s_rec;
   __shared__ u64 s_next;
-  __shared__ int s_ndistinct;
   __shared__ int s_overflow;
   __shared__ int s_fail;
   __shared__ int s_tcnt[NW];
@@ -488,7 +487,6 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 8)) k_scan_cta(
     if (qi >= nq) break;
     if (threadIdx.x == 0) {
       s_rec = q[qi];
-      s_ndistinct = 0;
       s_overflow = 0;
       s_fail = 0;
     }
@@ -504,7 +502,6 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 8)) k_scan_cta(
     const bool is_dense = (rec.w & kItemDense) != 0;
     const int logcap = (rec.w >> 8) & 0xff;
     const int nslots = 1 << logcap;
-    const int limit = (nslots * 3) / 4;
     const bool full_range = (rec.w & kItemWhole) || ((lo <= (MODE ? 0 : a + 1)) && hi >= A.n);
     const int span = hi - lo;
     const int e0 = A.off[a], e1 = A.off[a + 1];
@@ -541,12 +538,7 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 8)) k_scan_cta(
         scan_arcs<V>(s, len, w, A.idx, [&](int c, V wc) {
           if (MODE == 1 && c == a) return;
           if (*(volatile int*)&s_overflow) return;
-          const int rc = hash_add<V>(keys, vals, logcap, c, wc);
-          if (rc == 1) {
-            if (atomicAdd(&s_ndistinct, 1) >= limit) s_overflow = 1;
-          } else if (rc == 2) {
-            s_overflow = 1;
-          }
+          if (hash_add<V>(keys, vals, logcap, c, wc, fill_probes(logcap)) == 2) s_overflow = 1;
         });
         if (__any_sync(FULLMASK, *(volatile int*)&s_overflow != 0)) break;
       }
@@ -749,7 +741,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
   constexpr int H = THREADS / 2;                          // long entries [0, H), short [H, 2H)
   __shared__ int4 s_rec;
   __shared__ u64 s_next;
-  __shared__ int s_ndistinct, s_overflow, s_fail, s_qnl, s_qns;
+  __shared__ int s_overflow, s_fail, s_qnl, s_qns;
   __shared__ int s_tcnt[NW];
   __shared__ int2 s_wtot[NW];
   // optional phase profile (thread 0's clock): 0 item setup and boundary
@@ -808,7 +800,6 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
     // dense items sweep G windows; global-mode hash items G ranges
     const int G = (is_dense || MODE == 0) ? ((rec.w >> 16) & 0xfff) + 1 : 1;
     const int nslots = 1 << logcap;
-    const int limit = (nslots * 3) / 4;
     const int span = hi - lo;
     const int e0 = A.off[a], e1 = A.off[a + 1];
     const int K = e1 - e0;
@@ -845,7 +836,6 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
       const bool full_range =
           G == 1 && ((rec.w & kItemWhole) || (lo <= (MODE ? 0 : a + 1) && hi >= A.n));
       if (threadIdx.x == 0) {
-        s_ndistinct = 0;
         s_overflow = 0;
         s_qnl = 0;
         s_qns = 0;
@@ -879,12 +869,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_scan_big(ScanArgs A
           }
         } else {
           if (*(volatile int*)&s_overflow) return;
-          const int rc = hash_add<V>(keys, vals, logcap, c, wc);
-          if (rc == 1) {
-            if (atomicAdd(&s_ndistinct, 1) >= limit) s_overflow = 1;
-          } else if (rc == 2) {
-            s_overflow = 1;
-          }
+          if (hash_add<V>(keys, vals, logcap, c, wc, fill_probes(logcap)) == 2) s_overflow = 1;
         }
       };
       // phase A: one arc per thread, THREADS arcs at a time, dealt round-robin

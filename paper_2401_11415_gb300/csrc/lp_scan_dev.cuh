@@ -195,13 +195,22 @@ __device__ __forceinline__ u32 shared_add(V* p, V w) {
 }
 
 // Add w to key c (stored as c + 1).  Returns 1 if c was new, 0 if it
-// existed, 2 if the table had no free slot (bounded probe count).
+// existed, 2 if no free slot came within max_probe probes (by default the
+// whole table).  Tables that may fill pass fill_probes(logcap): a probe run
+// of a quarter of the table, at most 256 slots (linear probing,
+// multiplicative hash), means it is about three quarters full or more, and
+// the caller splits the range, so no shared distinct-key counter is needed.
+__device__ __forceinline__ u32 fill_probes(int logcap) {
+  return min(256u, (1u << logcap) >> 2);
+}
 template <typename V>
-__device__ __forceinline__ int hash_add(int* keys, V* vals, int logcap, int c, V w) {
+__device__ __forceinline__ int hash_add(int* keys, V* vals, int logcap, int c, V w,
+                                       u32 max_probe = 0xffffffffu) {
   const u32 mask = (1u << logcap) - 1u;
   const int key = c + 1;
   u32 h = hash_slot(key, logcap);
-  for (u32 probe = 0; probe <= mask; ++probe) {
+  const u32 np = min(mask, max_probe - 1u);
+  for (u32 probe = 0; probe <= np; ++probe) {
     const int k = ((volatile int*)keys)[h];
     if (k == key) {
       shared_add<V>(&vals[h], w);

@@ -53,7 +53,7 @@ __device__ bool serve_source(const SrvArgs& S, const SrvReq& R, int a, lp_link* 
   int* keys = reinterpret_cast<int*>(smem);
   V* vals = reinterpret_cast<V*>(smem + (size_t)kSrvSlots * 4);
   __shared__ unsigned long long s_w;
-  __shared__ int s_overflow, s_ndistinct, s_nstack, s_err, s_tcnt[kSrvWarps];
+  __shared__ int s_overflow, s_nstack, s_err, s_tcnt[kSrvWarps];
   __shared__ int2 s_stack[kSrvStack];
   const int lane = lane_id(), wid = threadIdx.x >> 5;
   const int cap = R.cap < 0 ? INT32_MAX : R.cap;
@@ -96,7 +96,6 @@ __device__ bool serve_source(const SrvArgs& S, const SrvReq& R, int a, lp_link* 
   TopEnt* top = tops + wid * R.k;
   int tcnt = 0;
   u64 n_cand = 0;
-  const int limit = (kSrvSlots * 3) / 4;
   if (W > 0) {
     // consecutive id ranges, each expected to fill at most half the table
     const u64 half = kSrvSlots / 2;
@@ -115,7 +114,6 @@ __device__ bool serve_source(const SrvArgs& S, const SrvReq& R, int a, lp_link* 
         if (threadIdx.x == 0) {
           s_nstack -= 1;
           s_overflow = 0;
-          s_ndistinct = 0;
         }
         __syncthreads();
         // insert the wedges with lo <= c < hi, c != a
@@ -138,12 +136,7 @@ __device__ bool serve_source(const SrvArgs& S, const SrvReq& R, int a, lp_link* 
           }
           scan_arcs<V>(s, len, wb, S.idx, [&](int c, V wc) {
             if (c == a || *(volatile int*)&s_overflow) return;
-            const int rc = hash_add<V>(keys, vals, kSrvLogcap, c, wc);
-            if (rc == 1) {
-              if (atomicAdd(&s_ndistinct, 1) >= limit) s_overflow = 1;
-            } else if (rc == 2) {
-              s_overflow = 1;
-            }
+            if (hash_add<V>(keys, vals, kSrvLogcap, c, wc, fill_probes(kSrvLogcap)) == 2) s_overflow = 1;
           });
           if (__any_sync(FULLMASK, *(volatile int*)&s_overflow != 0)) break;
         }
@@ -155,7 +148,7 @@ __device__ bool serve_source(const SrvArgs& S, const SrvReq& R, int a, lp_link* 
           }
           if (threadIdx.x == 0) {
             if (hi - lo < 2 || s_nstack + 2 > kSrvStack) {
-              // cannot happen: a range narrower than the fill limit fits
+              // cannot happen: one id never overflows, and each split halves
               *(volatile unsigned*)S.status = 1u;
               s_err = 1;
               s_nstack = 0;
