@@ -413,13 +413,13 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
       for (int rb0 = r0; rb0 < r1; rb0 += 128) {  // warp-uniform trips
         int cc[4];
         V ww[4];
+        int t = tt;  // the lane's run, carried from record to record (they rise)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int r = rb0 + 32 * k + lane;
           cc[k] = -1;
           ww[k] = 0;
           if (r < r1) {
-            int t = tt;
             while (s_pre[t + 1] <= r) ++t;
             const u64 at = s_rb[t] + (u64)(s_p0[t] + (r - s_pre[t]));
             if (V64) {
