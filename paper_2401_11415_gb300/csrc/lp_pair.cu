@@ -138,15 +138,34 @@ __global__ void k_scan_add(int2* __restrict__ sc, int n, const int2* __restrict_
   }
 }
 
-// Kept lists under a hub limit: kcnt[v] = |{b in Gamma_v : |Gamma_b| <= cap}|
-// (a warp per vertex), and after the scan of kcnt into koff the entries
-// themselves, in their order in Gamma_v.
+// Kept lists under a hub limit: kcnt[v] = |{b in Gamma_v : |Gamma_b| <= cap}|,
+// and after the scan of kcnt into koff the entries themselves, in their order
+// in Gamma_v.  A thread takes a vertex of degree at most kKeptThread (most
+// of them, so many short lists are read at once), a warp one of larger
+// degree; each kernel runs both passes and skips the other's vertices.
+constexpr int kKeptThread = 64;
+
 __global__ void k_kept_count(const int* __restrict__ off, const int* __restrict__ idx,
                              const int* __restrict__ deg, int n, int cap, int* __restrict__ kcnt) {
   const int lane = threadIdx.x & 31;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int nthreads = gridDim.x * blockDim.x;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += nthreads) {
+    const int e0 = off[v], e1 = off[v + 1];
+    if (e1 - e0 > kKeptThread) continue;
+    int c = 0, e = e0;
+    for (; e + 4 <= e1; e += 4) {  // four list entries, then their degrees, in flight
+      const int b0 = __ldg(idx + e), b1 = __ldg(idx + e + 1), b2 = __ldg(idx + e + 2),
+                b3 = __ldg(idx + e + 3);
+      c += (__ldg(deg + b0) <= cap) + (__ldg(deg + b1) <= cap) + (__ldg(deg + b2) <= cap) +
+           (__ldg(deg + b3) <= cap);
+    }
+    for (; e < e1; ++e) c += __ldg(deg + __ldg(idx + e)) <= cap ? 1 : 0;
+    kcnt[v] = c;
+  }
+  const int nwarps = nthreads >> 5;
   for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nwarps) {
     const int e0 = off[v], e1 = off[v + 1];
+    if (e1 - e0 <= kKeptThread) continue;  // warp-uniform
     int c = 0;
     for (int e = e0 + lane; e < e1; e += 32) c += __ldg(deg + __ldg(idx + e)) <= cap ? 1 : 0;
     c = (int)__reduce_add_sync(FULLMASK, (u32)c);
@@ -158,9 +177,28 @@ __global__ void k_kept_scatter(const int* __restrict__ off, const int* __restric
                                const int* __restrict__ deg, int n, int cap,
                                const int2* __restrict__ koff, int* __restrict__ kidx) {
   const int lane = threadIdx.x & 31;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int nthreads = gridDim.x * blockDim.x;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += nthreads) {
+    const int e0 = off[v], e1 = off[v + 1];
+    if (e1 - e0 > kKeptThread) continue;
+    int o = koff[v].x, e = e0;
+    for (; e + 4 <= e1; e += 4) {
+      const int b[4] = {__ldg(idx + e), __ldg(idx + e + 1), __ldg(idx + e + 2), __ldg(idx + e + 3)};
+      const bool k[4] = {__ldg(deg + b[0]) <= cap, __ldg(deg + b[1]) <= cap,
+                         __ldg(deg + b[2]) <= cap, __ldg(deg + b[3]) <= cap};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (k[j]) kidx[o++] = b[j];
+    }
+    for (; e < e1; ++e) {
+      const int b = __ldg(idx + e);
+      if (__ldg(deg + b) <= cap) kidx[o++] = b;
+    }
+  }
+  const int nwarps = nthreads >> 5;
   for (int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nwarps) {
     const int e0 = off[v], e1 = off[v + 1];
+    if (e1 - e0 <= kKeptThread) continue;  // warp-uniform
     int o = koff[v].x;
     for (int eb = e0; eb < e1; eb += 32) {  // warp-uniform trips
       const int e = eb + lane;
@@ -187,19 +225,35 @@ constexpr int kSmallLinks = 64;
 constexpr int kSmallLog = 10;
 constexpr int kSmallWarps = 8;  // per 256-thread CTA: 32 KB of tables
 
-// groups[g] = (u, first position in perm, links of u), warp groups from the
-// front (count nsg[0]), CTA groups from the back (count nsg[1]); cnt: the
+// A CTA group of more links is cut into parts of kGroupLinks links, each a
+// CTA's (it marks the owner's list again), so that a hub with a hundred
+// thousand links is not one CTA's long tail.
+constexpr int kGroupLinks = 4096;
+
+// Entries of groups (gcap of them): n + links / kGroupLinks + 1 bound the
+// warp groups and CTA group parts together.
+static inline size_t pair_group_cap(int n, u64 nlinks) {
+  return (size_t)n + nlinks / kGroupLinks + 1;
+}
+
+// groups[g] = (u, first position in perm, links), warp groups from the front
+// (count nsg[0]), CTA group parts from the back (count nsg[1]); cnt: the
 // histogram (kept apart from the scanned array sc).
 __global__ void k_pair_groups(const int* __restrict__ cnt, const int2* __restrict__ sc,
                               const int* __restrict__ off, int n, int4* __restrict__ groups,
-                              u32* __restrict__ nsg) {
+                              long long gcap, u32* __restrict__ nsg) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   if (u < n && cnt[u] > 0) {
-    const int4 G = make_int4(u, sc[u].x, cnt[u], 0);
-    if (off[u + 1] - off[u] <= kSmallDeg && cnt[u] <= kSmallLinks)
-      groups[atomicAdd(&nsg[0], 1u)] = G;
-    else
-      groups[n - 1 - (int)atomicAdd(&nsg[1], 1u)] = G;
+    const int c = cnt[u], first = sc[u].x;
+    if (off[u + 1] - off[u] <= kSmallDeg && c <= kSmallLinks) {
+      groups[atomicAdd(&nsg[0], 1u)] = make_int4(u, first, c, 0);
+    } else {
+      const int parts = (c + kGroupLinks - 1) / kGroupLinks;
+      const long long at = (long long)atomicAdd(&nsg[1], (u32)parts);
+      for (int j = 0; j < parts; ++j)
+        groups[gcap - 1 - (at + j)] =
+            make_int4(u, first + j * kGroupLinks, min(kGroupLinks, c - j * kGroupLinks), 0);
+    }
   }
 }
 
@@ -314,7 +368,7 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
                                                             const int* __restrict__ foff,
                                                             const int* __restrict__ fidx,
                                                             const int* __restrict__ deg,
-                                                            int nwords, int n,
+                                                            int nwords, int n, long long gcap,
                                                             u32* __restrict__ claim,
                                                             int* __restrict__ cur) {
   extern __shared__ u32 bits[];
@@ -339,7 +393,7 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
     __syncthreads();
     const u32 gi = s_g;
     if (gi >= ngroups) break;
-    const int4 G = groups[n - 1 - (int)gi];
+    const int4 G = groups[gcap - 1 - (long long)gi];
     const int u = G.x, e0 = off[u], e1 = off[u + 1];
     // Two ways to count: walk every link's list (the sum of their lengths),
     // or expand the wedges of u once per chunk of links (the kept b of u,
@@ -528,15 +582,15 @@ __global__ void __launch_bounds__(1024, 1) k_pair_cn_groups(lp_link* __restrict_
 }
 
 // Scratch layout: sc int2[n + 1], cnt int[n + 1], perm int[links], groups
-// int4[n], sums int2[chunks], claim u32, window cursors int[links]; under a
-// hub limit also the kept lists: koff int[n + 1] and kidx int[arcs]; every
-// part 256-byte aligned (groups are written as int4).
+// int4[n + links / kGroupLinks + 1], sums int2[chunks], claim u32, window
+// cursors int[links]; under a hub limit also the kept lists: koff int[n + 1]
+// and kidx int[arcs]; every part 256-byte aligned (groups are int4).
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t pair_groups_scratch(int n, u64 nlinks, long long kept_arcs) {
   const size_t n1 = (size_t)n + 1;
   size_t b = align256(n1 * sizeof(int2)) + align256(n1 * sizeof(int)) +
-             align256(nlinks * sizeof(int)) + align256((size_t)n * sizeof(int4)) +
+             align256(nlinks * sizeof(int)) + align256(pair_group_cap(n, nlinks) * sizeof(int4)) +
              align256(((n1 + kScanChunk - 1) / kScanChunk) * sizeof(int2)) + 256 +
              align256(nlinks * sizeof(int));
   if (kept_arcs > 0) b += align256(n1 * sizeof(int)) + align256((size_t)kept_arcs * sizeof(int));
@@ -560,7 +614,8 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
   int* perm = reinterpret_cast<int*>(p);
   p += align256(n * sizeof(int));
   int4* groups = reinterpret_cast<int4*>(p);
-  p += align256((size_t)nv * sizeof(int4));
+  const long long gcap = (long long)pair_group_cap(nv, n);
+  p += align256((size_t)gcap * sizeof(int4));
   const int nb = (n1 + kScanChunk - 1) / kScanChunk;
   int2* sums = reinterpret_cast<int2*>(p);
   p += align256((size_t)nb * sizeof(int2));
@@ -578,7 +633,7 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
     int* koff = reinterpret_cast<int*>(p);
     p += align256((size_t)n1 * sizeof(int));
     int* kidx = reinterpret_cast<int*>(p);
-    const int wb = nsm * 8;  // 256-thread blocks, a warp per vertex
+    const int wb = nsm * 8;  // 256-thread blocks
     k_kept_count<<<wb, 256, 0, st>>>(off, idx, deg, nv, cap, cnt);
     e = cudaMemsetAsync(cnt + nv, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -602,7 +657,7 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
   k_scan_counts<<<nb, kScanThreads, 0, st>>>(cnt, n1, sc, sums);
   k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, nb);
   k_scan_add<<<(n1 + 255) / 256, 256, 0, st>>>(sc, n1, sums);
-  k_pair_groups<<<(nv + 255) / 256, 256, 0, st>>>(cnt, sc, off, nv, groups, claim + 2);
+  k_pair_groups<<<(nv + 255) / 256, 256, 0, st>>>(cnt, sc, off, nv, groups, gcap, claim + 2);
   k_pair_scatter<<<gb, 256, 0, st>>>(links, n, off, sc, perm);
   // a bitmap over every vertex when it fits in 224 KB, else windows of that
   // size (and room for the hash set)
@@ -614,7 +669,7 @@ cudaError_t launch_pair_cn_groups(lp_link* links, u64 n, int nv, const int* off,
   k_pair_cn_small<<<nsm * 7, kSmallWarps * 32, 0, st>>>(links, perm, groups, claim + 2, off, idx,
                                                         claim + 1);
   k_pair_cn_groups<<<nsm, 1024, smem, st>>>(links, perm, groups, claim + 2, off, idx, foff, fidx,
-                                            deg, nwords, nv, claim, cur);
+                                            deg, nwords, nv, gcap, claim, cur);
   if (launches) *launches += 8;
   return cudaGetLastError();
 }

@@ -106,6 +106,10 @@ def test_pair_counts_large_groups(lp):
     for m in ("AA", "RA"):
         for cap in (None, 64, 16):
             check_global(lp, g, m, cap, 150000)
+    # a hub owning more than 4096 links: its group is cut into parts, one CTA each
+    g = L.chung_lu(20000, 10.0, 2.1, dmax=6000, seed=22)
+    check_global(lp, g, "RA", None, 300000)
+    check_global(lp, g, "AA", 64, 300000)
 
 
 def test_degenerate_graphs(lp):
