@@ -244,15 +244,18 @@ typedef enum {
   LP_OPT_BIG_CTA_THREADS = 9, /* threads of a large-tier CTA: 1024 (one per SM,
                                  192 KB table) or 512 (two per SM, 98 KB each;
                                  split targets shrink with the table) (1024)   */
-  LP_OPT_EXPAND = 10,         /* global mode: large sources that would be cut
-                                 into several id-range items are instead
+  LP_OPT_EXPAND = 10,         /* global mode: large sources with more wedges
+                                 than LP_OPT_EXPAND_MIN_WEDGES are instead
                                  expanded once into per-bucket records and
                                  counted bucket by bucket: 0 never, 1 always,
                                  2 when the index array exceeds 128 MB (2)     */
   LP_OPT_EXPAND_BATCH = 11,   /* wedges expanded per batch of that tier
                                  (2^16..2^34, 2^29; 4 bytes each, 8 for AA/RA) */
-  LP_OPT_EXPAND_HASH_LOGCAP = 12 /* log2 slots of that tier's hash tables (6..14,
+  LP_OPT_EXPAND_HASH_LOGCAP = 12, /* log2 slots of that tier's hash tables (6..14,
                                  14); a bucket whose table fills is re-split */
+  LP_OPT_EXPAND_MIN_WEDGES = 13, /* that tier takes the large sources with more
+                                 wedges than this (257..2^30; at least the
+                                 medium-tier limit) (8192)                     */
 } lp_option;
 
 /*

@@ -310,7 +310,7 @@ def lp_predict_sources_static(h, measure, d_sources, n_src: int, k: int, degree_
 LP_OPT_SELECT_BUFFER, LP_OPT_WARP_MAX_WEDGES, LP_OPT_CTA_MAX_WEDGES, LP_OPT_SPLIT_TARGET, \
     LP_OPT_SPLIT_LOGCAP, LP_OPT_MED_MAX_WEDGES, LP_OPT_ITEM_WEDGES, LP_OPT_PHASE_PROFILE, \
     LP_OPT_BIG_CTA_THREADS, LP_OPT_EXPAND, LP_OPT_EXPAND_BATCH, \
-    LP_OPT_EXPAND_HASH_LOGCAP = range(1, 13)
+    LP_OPT_EXPAND_HASH_LOGCAP, LP_OPT_EXPAND_MIN_WEDGES = range(1, 14)
 
 
 def lp_set_option(option: int, value: int) -> None:

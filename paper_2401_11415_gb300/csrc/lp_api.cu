@@ -201,6 +201,10 @@ lp_status lp_set_option(lp_option option, int64_t value) {
       if (value < 6 || value > 14) break;
       lp::g_opt.expand_logcap = (int)value;
       return LP_OK;
+    case LP_OPT_EXPAND_MIN_WEDGES:
+      if (value < 257 || value > (1ll << 30)) break;
+      lp::g_opt.expand_min = (int)value;
+      return LP_OK;
     case LP_OPT_CTA_MAX_WEDGES:
       if (value < 257 || value > lp::kCtaMaxWedges) break;
       lp::g_opt.cta_max = (int)value;
@@ -235,6 +239,7 @@ int64_t lp_get_option(lp_option option) {
     case LP_OPT_EXPAND: return o.expand;
     case LP_OPT_EXPAND_BATCH: return o.expand_batch;
     case LP_OPT_EXPAND_HASH_LOGCAP: return o.expand_logcap;
+    case LP_OPT_EXPAND_MIN_WEDGES: return o.expand_min;
     default: return -1;
   }
 }
@@ -745,6 +750,7 @@ static lp_status predict_global(Graph& g, int measure, int cap, int64_t k, doubl
   A.expand = opt.expand == 1 || (opt.expand == 2 && g.arcs * (int64_t)sizeof(int) > (128ll << 20));
   // the count pass's 64 KB table holds 8192 slots of 32-bit values, 4096 of 64-bit
   A.x_logcap = std::min(opt.expand_logcap, (measure == LP_AA || measure == LP_RA) ? 12 : 13);
+  A.x_min = std::max(opt.expand_min, A.med_max);
   // selection buffer
   const u64 minbuf = (u64)std::max<long long>(16, options_snapshot().select_buffer);
   u64 C = k > 0 ? std::max<u64>(minbuf, 2ull * (u64)k + std::min<u64>(minbuf, 1ull << 20)) : minbuf;

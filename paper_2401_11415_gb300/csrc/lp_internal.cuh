@@ -180,6 +180,7 @@ struct ScanArgs {
   // expand-and-count tier (global mode)
   int expand;          // 1: large sources with W > cta_max become units (when W < 2^31)
   int x_logcap;        // log2 slots of a hash bucket's table
+  int x_min;           // large sources with more wedges than this are units
   int4* xq;            // estimate output: unit records {a, lo, hi, kept}
   u64* xw;             // and their wedge counts
   u64 xq_cap;
@@ -205,6 +206,7 @@ struct Options {
   int expand = 2;                  // 0 off, 1 on, 2 when the index array exceeds 128 MB
   long long expand_batch = 1ll << 29;  // wedges expanded per batch
   int expand_logcap = 14;          // log2 slots of the count pass's hash tables
+  int expand_min = 8192;           // smallest units (wedges, exclusive)
 };
 Options options_snapshot();
 

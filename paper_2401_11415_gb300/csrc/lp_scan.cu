@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256) k_estimate(ScanArgs A, int n_rec, int4* _
     if (valid && W > 0) tier = W <= (u64)A.warp_max ? 0 : (W <= (u64)A.med_max ? 1 : 2);
     // global mode: a large source that would be cut into several items is
     // expanded and counted by bucket instead (wedge offsets are 32-bit)
-    if (MODE == 0 && tier == 2 && A.expand && W > (u64)A.cta_max && W < (1ull << 31)) tier = 3;
+    if (MODE == 0 && tier == 2 && A.expand && W > (u64)A.x_min && W < (1ull << 31)) tier = 3;
     if (tier >= 0) {
       ts.w[tier] += W;
       ts.a[tier] += (u64)(e1 - e0);
