@@ -281,24 +281,51 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
   __shared__ int2 s_wsum[NW];
   __shared__ int4 s_rec, s_rec_next;
   __shared__ ExpUnit s_unit, s_unit_next;
+  __shared__ int s_p0n[kExpMaxTiles], s_lenn[kExpMaxTiles];  // the next item's runs
+  __shared__ u64 s_rbn[kExpMaxTiles];
   __shared__ u64 s_next;
-  __shared__ int s_overflow, s_fail, s_e0, s_e1;
+  __shared__ int s_overflow, s_fail, s_e0, s_e1, s_e0n, s_e1n;
   const int lane = lane_id(), wid = threadIdx.x >> 5;
   for (int i = threadIdx.x * 16; i < kExpTableBytes; i += kCountThreads * 16)
     *reinterpret_cast<int4*>(smem + i) = make_int4(0, 0, 0, 0);
   const Thresh T = *A.thresh;
   u64 n_cand = 0;
-  // claim and fetch (record, unit) of an item; thread 0 only
-  auto fetch = [&](u64 qi, int4& r, ExpUnit& U) {
-    if (qi < nq) {
-      r = q[qi];
-      U = A.xunit[A.xbucket_unit[r.w & kExpGbMask]];
+  // warp 0: claim the next item and load its record, unit, run of every tile
+  // and slice of Gamma_a, so that none of these chains of dependent loads
+  // lies on the path of the item after it
+  auto prefetch = [&]() {
+    if (lane == 0) {
+      const u64 nx = *(volatile u32*)&A.ctr->full ? ~0ull : atomicAdd(claim, 1ull);
+      s_next = nx;
+      if (nx < nq) {
+        s_rec_next = q[nx];
+        s_unit_next = A.xunit[A.xbucket_unit[s_rec_next.w & kExpGbMask]];
+      }
+    }
+    __syncwarp();
+    if (s_next >= nq) return;  // warp-uniform
+    const int4 r = s_rec_next;
+    const ExpUnit& U = s_unit_next;
+    const int bb = (int)((r.w & kExpGbMask) - U.bucket_base);
+    for (int tt = lane; tt < U.T; tt += 32) {
+      const int* pt = A.xpre + U.pre_base + (long long)tt * (U.nb + 1) + bb;
+      const int p0 = pt[0];
+      s_p0n[tt] = p0;
+      s_lenn[tt] = pt[1] - p0;
+      s_rbn[tt] = A.xtile_rec[U.tile_base + tt];
+    }
+    if (lane == 0) {
+      const int* ex = A.xexcl + U.excl_base + bb;
+      int e0 = ex[0], e1 = ex[1];
+      if (r.w & kExpSplit) {  // a part of the bucket: narrow the slice
+        e0 = lower_bound_g(A.idx, e0, e1, max(r.y, r.x + 1));
+        e1 = lower_bound_g(A.idx, e0, e1, r.z);
+      }
+      s_e0n = e0;
+      s_e1n = e1;
     }
   };
-  if (threadIdx.x == 0) {
-    s_next = *(volatile u32*)&A.ctr->full ? ~0ull : atomicAdd(claim, 1ull);
-    fetch(s_next, s_rec_next, s_unit_next);
-  }
+  if (wid == 0) prefetch();
   __syncthreads();
   for (;;) {
     const u64 qi = s_next;
@@ -306,6 +333,8 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
     if (threadIdx.x == 0) {
       s_rec = s_rec_next;
       s_unit = s_unit_next;
+      s_e0 = s_e0n;
+      s_e1 = s_e1n;
       s_fail = 0;
       s_overflow = 0;
     }
@@ -323,27 +352,16 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
     const int limit = (nslots * 3) / 4;
     u32* dlo = words;
     u32* dhi = words + (1 << wlog);
-    // the bucket's run in every tile (one per thread) and their prefix; the
-    // slice of Gamma_a in the bucket
+    (void)b;
+    // the bucket's run in every tile (one per thread; loaded ahead) and
+    // their prefix
     {
       int len = 0;
       const int tt = threadIdx.x;
       if (tt < nt) {
-        const int* pt = A.xpre + U.pre_base + (long long)tt * (U.nb + 1) + b;
-        const int p0 = pt[0];
-        len = pt[1] - p0;
-        s_p0[tt] = p0;
-        s_rb[tt] = A.xtile_rec[U.tile_base + tt];
-      }
-      if (threadIdx.x == 0) {
-        const int* ex = A.xexcl + U.excl_base + b;
-        int e0 = ex[0], e1 = ex[1];
-        if (rec.w & kExpSplit) {  // a part of the bucket: narrow the slice
-          e0 = lower_bound_g(A.idx, e0, e1, max(clo, a + 1));
-          e1 = lower_bound_g(A.idx, e0, e1, chi);
-        }
-        s_e0 = e0;
-        s_e1 = e1;
+        len = s_lenn[tt];
+        s_p0[tt] = s_p0n[tt];
+        s_rb[tt] = s_rbn[tt];
       }
       int incl = len;
 #pragma unroll
@@ -364,10 +382,7 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
       if (threadIdx.x == 0) s_pre[nt] = total;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {  // look-ahead: claim and fetch the next item while this one runs
-      s_next = *(volatile u32*)&A.ctr->full ? ~0ull : atomicAdd(claim, 1ull);
-      fetch(s_next, s_rec_next, s_unit_next);
-    }
+    if (wid == 0) prefetch();  // the next item, while this one is counted
     // a table that receives at most `limit` records stays at most three
     // quarters full: then it is probed to the end and never overflows
     const int R = s_pre[nt];
@@ -409,36 +424,34 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
         }
         tt = l;
       }
-      // 128 records per step, four loads in flight per lane before any insert
-      for (int rb0 = r0; rb0 < r1; rb0 += 128) {  // warp-uniform trips
-        int cc[4];
-        V ww[4];
+      // 256 records per step, eight loads in flight per lane before any insert
+      for (int rb0 = r0; rb0 < r1; rb0 += 256) {  // warp-uniform trips
+        int cc[8], dd[8];
         int t = tt;  // the lane's run, carried from record to record (they rise)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 8; ++k) {
           const int r = rb0 + 32 * k + lane;
           cc[k] = -1;
-          ww[k] = 0;
+          dd[k] = 0;
           if (r < r1) {
             while (s_pre[t + 1] <= r) ++t;
             const u64 at = s_rb[t] + (u64)(s_p0[t] + (r - s_pre[t]));
             if (V64) {
               const int2 x = reinterpret_cast<const int2*>(A.xrec)[at];
               cc[k] = x.x;
-              ww[k] = (V)x.y;  // |Gamma_b| until the weight lookup below
+              dd[k] = x.y;  // |Gamma_b|, for the weight lookup below
             } else {
               cc[k] = reinterpret_cast<const int*>(A.xrec)[at];
-              ww[k] = (V)1;
             }
           }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 8; ++k) {
           const int c = cc[k];
-          if (c >= clo && c < chi) insert(c, V64 ? (V)__ldg(A.wt + (int)ww[k]) : (V)1);
+          if (c >= clo && c < chi) insert(c, V64 ? (V)__ldg(A.wt + dd[k]) : (V)1);
         }
         // the run of the warp's next first record
-        const int rn = min(rb0 + 128, r1 - 1);
+        const int rn = min(rb0 + 256, r1 - 1);
         while (tt + 1 < nt && s_pre[tt + 1] <= rn) ++tt;
         if (guard && *(volatile int*)&s_overflow) break;
       }
