@@ -127,18 +127,24 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_record(kernel: str):
+def traffic_record(kernel: str, alg_bytes_per_launch: float):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources."""
+    the current kernel sources: the measured DRAM bytes per algorithmic byte
+    of the captured launches (every launch of the kernel in one call) times
+    this run's algorithmic bytes per launch.  (None, None) otherwise."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))
     except Exception:
-        return None
+        return None, None
     ent = rec.get(kernel)
     if not ent or ent.get("kernel_hash") != kernel_hash():
-        return None
-    return ent.get("dram_bytes_per_launch")
+        return None, None
+    ratio = ent.get("dram_bytes_per_alg_byte")
+    if ratio is None:
+        return None, None
+    return int(ratio * alg_bytes_per_launch), (
+        f"{ratio:.4f} DRAM bytes per algorithmic byte, measured by ncu on {ent.get('workload')}")
 
 
 _ARGS = None
@@ -284,9 +290,11 @@ def roofline(stats):
     avg_ms = tier_ms[dom] / launches
     peak, peak_kind = peaks()
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+    traffic, basis = traffic_record(name, bytes_per_launch)
     return {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": peak,
             "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-            "traffic": traffic_record(name), "alg_bytes_per_launch": int(bytes_per_launch),
+            "traffic": traffic, "traffic_basis": basis,
+            "alg_bytes_per_launch": int(bytes_per_launch),
             "avg_launch_ms": round(avg_ms, 4), "launches": int(launches),
             "share_of_scan_ms": round(tier_ms[dom] / max(1e-9, sum(tier_ms)), 4)}
 

@@ -41,15 +41,17 @@ def test_traffic_record_follows_kernel_hash(tmp_path, monkeypatch):
     h = b.kernel_hash()
     assert h == b.kernel_hash() and len(h) == 16
     (tmp_path / "profiles").mkdir()
-    rec = {"k_scan_big": {"kernel_hash": h, "dram_bytes_per_launch": 1234}}
+    rec = {"k_scan_big": {"kernel_hash": h, "dram_bytes_per_alg_byte": 0.25,
+                          "workload": "a test"}}
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(b, "ROOT", str(tmp_path))
     # the hash is taken over the sources under ROOT: point it back at the repository's
     monkeypatch.setattr(b, "kernel_hash", lambda: h)
-    assert b.traffic_record("k_scan_big") == 1234
-    assert b.traffic_record("k_scan_cta") is None
+    t, basis = b.traffic_record("k_scan_big", 4000)
+    assert t == 1000 and "a test" in basis
+    assert b.traffic_record("k_scan_cta", 4000) == (None, None)
     monkeypatch.setattr(b, "kernel_hash", lambda: "0" * 16)
-    assert b.traffic_record("k_scan_big") is None
+    assert b.traffic_record("k_scan_big", 4000) == (None, None)
 
 
 def test_roofline_picks_dominant_tier_and_counts_its_bytes():
