@@ -118,12 +118,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# the sources the global mode's kernels and their launches are built from
+# (the serving, batched and allocation-free paths are not among them)
+GLOBAL_PATH_SOURCES = ["lp_internal.cuh", "lp_scan_dev.cuh", "lp_scan.cu", "lp_expand.cu",
+                       "lp_select.cu", "lp_sort.cu", "lp_pair.cu", "lp_api.cu"]
+
+
 def kernel_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2401_11415_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in GLOBAL_PATH_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -228,7 +228,16 @@ __global__ void __launch_bounds__(kSrvThreads, 2) k_serve(SrvArgs S) {
   __shared__ SrvReq s_req;
   for (int i = threadIdx.x * 16; i < kSrvSlots * (4 + 8); i += kSrvThreads * 16)
     *reinterpret_cast<int4*>(smem + i) = make_int4(0, 0, 0, 0);
-  int idle = 0;
+  // Idle polls back off from 1 us to 128 us: every poll reads host memory
+  // over the chip-to-chip link, and hundreds of CTAs polling every few
+  // microseconds slowed the CTAs that had work (their sources and rows live
+  // in host memory too).  The kernel leaves after idle_polls x 4 us without
+  // work.  The request record is re-read only when the claimed item belongs
+  // to another request than the CTA's last one.
+  unsigned long long idle_ns = 0;
+  unsigned nap = 1000;
+  int last_req = -1;
+  unsigned long long last_seq = 0;
   for (;;) {
     if (threadIdx.x == 0) {
       s_have = 0;
@@ -242,16 +251,22 @@ __global__ void __launch_bounds__(kSrvThreads, 2) k_serve(SrvArgs S) {
           const int2 it = make_int2(ip[0], ip[1]);
           s_item = it;
           const volatile SrvReq* rq = S.reqs + it.x;
-          SrvReq r;
-          r.measure = rq->measure;
-          r.cap = rq->cap;
-          r.k = rq->k;
-          r.n_src = rq->n_src;
-          r.src_off = rq->src_off;
-          r.out_off = rq->out_off;
-          r.target = rq->target;
-          r.seq = rq->seq;
-          s_req = r;
+          // a slot is reused by later requests: its sequence number tells
+          const unsigned long long seq = rq->seq;
+          if (it.x != last_req || seq != last_seq) {
+            SrvReq r;
+            r.measure = rq->measure;
+            r.cap = rq->cap;
+            r.k = rq->k;
+            r.n_src = rq->n_src;
+            r.src_off = rq->src_off;
+            r.out_off = rq->out_off;
+            r.target = rq->target;
+            r.seq = seq;
+            s_req = r;
+            last_req = it.x;
+            last_seq = seq;
+          }
           s_have = 1;
           break;
         }
@@ -259,12 +274,15 @@ __global__ void __launch_bounds__(kSrvThreads, 2) k_serve(SrvArgs S) {
     }
     __syncthreads();
     if (!s_have) {  // CTA-uniform
-      if (++idle > S.idle_polls || s_stop) break;
-      if (threadIdx.x == 0) __nanosleep(4000);
+      idle_ns += nap;
+      if (idle_ns > (unsigned long long)S.idle_polls * 4000ull || s_stop) break;
+      if (threadIdx.x == 0) __nanosleep(nap);
+      nap = min(2u * nap, 128000u);
       __syncthreads();
       continue;
     }
-    idle = 0;
+    idle_ns = 0;
+    nap = 1000;
     const int2 it = s_item;
     const SrvReq R = s_req;
     const int a = *(const volatile int*)(S.src_pool + R.src_off + it.y);
