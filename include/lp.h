@@ -348,15 +348,19 @@ typedef struct {
   int32_t paused;            /* 1: queue requests but start no batch until
                                 lp_serve_resume                                   */
   int32_t mode;              /* 0: host worker threads run batches (the default);
-                                1: a resident kernel serves the requests; it
-                                defers sources above defer_wedges to a host
-                                thread running the tiered pipeline             */
-  int32_t idle_polls;        /* mode 1: polls (about 4 us apart) a resident CTA
-                                waits for work before it leaves (0: 2500)        */
+                                1: a resident kernel serves the requests (it can
+                                defer sources above defer_wedges to a host
+                                thread running the tiered pipeline)            */
+  int32_t idle_polls;        /* mode 1: the kernel is asked to leave once no work
+                                has been outstanding for idle_polls x 4 us, and
+                                a CTA leaves on its own after 100 times that
+                                without work (0: 2500)                           */
   int32_t defer_wedges;      /* mode 1: a source with more wedges than this (its
                                 hub-limited two-hop work) is not counted by the
                                 resident kernel but by the tiered per-source
-                                pipeline when its request is collected (0: 65536) */
+                                pipeline when its request is collected; the
+                                kernel leaves the GPU to that pipeline until
+                                those rows are in (0: 65536)                    */
 } lp_serve_opts;
 
 typedef struct {

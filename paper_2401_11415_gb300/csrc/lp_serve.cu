@@ -23,11 +23,14 @@
 // (4 + 16 k bytes per source) fit in the pools, a slot is free and the ring
 // has room.  Finished requests are collected by any call that polls (submit,
 // wait, poll): their rows are copied out and their memory freed, so waiting
-// requests are admitted as memory frees up.  The kernel leaves when it finds
-// no work for idle_polls polls; a call that sees published work and no kernel
-// running launches it again.  Sources with more than defer_wedges wedges are
-// left by the kernel to a host thread that runs them through the tiered
-// pipeline in batches.
+// requests are admitted as memory frees up.  The kernel leaves as a whole:
+// once no work has been outstanding for idle_polls x 4 us, a polling call sets
+// the stop word, and clears it when the kernel has ended; a call that sees
+// published work and no kernel running launches it again.  Sources with more
+// than defer_wedges wedges are left by the kernel to a host thread that runs
+// them through the tiered pipeline in batches; while such rows wait, the
+// kernel is asked to leave, so the pipeline has the whole GPU, and it is
+// launched again after them.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -128,9 +131,14 @@ struct DevLoop {
   std::deque<Request*> waiting;  // submitted, not admitted yet
   std::vector<Request*> inflight;
   std::deque<Request*> dq;        // waiting for their deferred rows
+  bool dbusy = false;             // dthread is running a batch of them
+  std::chrono::steady_clock::time_point launched_at;
   std::thread dthread;            // runs the deferred rows in batches
   bool dstop = false;             // ends dthread (set after the last request)
   bool running = false;
+  bool stopping = false;  // the stop word is set for lack of work (not by close)
+  bool idle_seen = false; // no outstanding work since idle_since
+  std::chrono::steady_clock::time_point idle_since;
   unsigned next_seq = 1;
 };
 
@@ -354,22 +362,60 @@ cudaError_t dev_open(lp_server* S) {
 // S->mu held in every helper below.
 
 // Launch the resident kernel if work is outstanding and it is not running.
+// The longest the resident kernel runs while deferred rows wait.
+constexpr std::chrono::milliseconds kDeferPeriod(10);
+
 void dev_ensure_running(lp_server* S) {
   DevLoop& D = S->dev;
-  if (D.published == D.retired) return;
+  const bool work = D.published != D.retired;
+  const auto now = std::chrono::steady_clock::now();
   if (D.running) {
     const cudaError_t q = cudaStreamQuery(D.stream);
-    if (q == cudaErrorNotReady) return;
+    if (q == cudaErrorNotReady) {
+      // deferred sources waiting for the tiered pipeline: once the kernel
+      // has run for kDeferPeriod it gives the GPU up to them (its CTAs leave
+      // after their current source); the pipeline runs while no kernel does
+      if (!D.dq.empty() && !D.stopping && now - D.launched_at >= kDeferPeriod) {
+        __atomic_store_n(D.stop, 1u, __ATOMIC_RELEASE);
+        D.stopping = true;
+        return;
+      }
+      // the kernel leaves as a whole: after idle_polls x 4 us with no work
+      // outstanding the host sets the stop word, and clears it only once the
+      // kernel has ended (new work waits for the next launch)
+      if (work) {
+        D.idle_seen = false;
+      } else if (!D.stopping) {
+        if (!D.idle_seen) {
+          D.idle_seen = true;
+          D.idle_since = now;
+        } else if (now - D.idle_since >
+                   std::chrono::microseconds(4ll * S->opts.idle_polls)) {
+          __atomic_store_n(D.stop, 1u, __ATOMIC_RELEASE);
+          D.stopping = true;
+        }
+      }
+      return;
+    }
     D.running = false;
+    D.idle_seen = false;
+    if (D.stopping) {
+      __atomic_store_n(D.stop, 0u, __ATOMIC_RELEASE);
+      D.stopping = false;
+    }
+    S->cv_work.notify_all();  // the deferred thread waits for the kernel to end
     if (q != cudaSuccess) {
       cudaGetLastError();
       __atomic_store_n(D.status, 2u, __ATOMIC_RELEASE);  // the kernel failed
       return;
     }
   }
-  if (__atomic_load_n(D.status, __ATOMIC_ACQUIRE) != 0) return;
+  // no launch while the deferred thread runs a batch or is about to start one
+  if (!work || D.dbusy || !D.dq.empty() || __atomic_load_n(D.status, __ATOMIC_ACQUIRE) != 0)
+    return;
   if (lp::launch_serve(D.args, S->opts.max_k, D.stream) == cudaSuccess) {
     D.running = true;
+    D.launched_at = now;
     S->stats.kernel_launches += 1;
   } else {
     cudaGetLastError();
@@ -433,7 +479,8 @@ void dev_deferred_main(lp_server* S) {
     srcs.clear();
     {
       std::unique_lock<std::mutex> lock(S->mu);
-      S->cv_work.wait(lock, [&] { return D.dstop || !D.dq.empty(); });
+      // a batch starts when no resident kernel runs (it gives the GPU up)
+      S->cv_work.wait(lock, [&] { return D.dstop || (!D.dq.empty() && !D.running); });
       if (D.dq.empty()) return;  // stopped and drained
       Request* first = D.dq.front();
       for (auto it = D.dq.begin(); it != D.dq.end();) {
@@ -448,6 +495,7 @@ void dev_deferred_main(lp_server* S) {
           ++it;
         }
       }
+      D.dbusy = true;
     }
     const int nd = (int)srcs.size(), k = first_k(batch);
     D.h_dout.resize((size_t)nd * k);
@@ -493,6 +541,7 @@ void dev_deferred_main(lp_server* S) {
         S->stats.completed += 1;
       }
       S->stats.deferred_sources += nd;
+      D.dbusy = false;
     }
     S->cv_done.notify_all();
   }

@@ -229,11 +229,13 @@ __global__ void __launch_bounds__(kSrvThreads, 2) k_serve(SrvArgs S) {
   for (int i = threadIdx.x * 16; i < kSrvSlots * (4 + 8); i += kSrvThreads * 16)
     *reinterpret_cast<int4*>(smem + i) = make_int4(0, 0, 0, 0);
   // Idle polls back off from 1 us to 128 us: every poll reads host memory
-  // over the chip-to-chip link, and hundreds of CTAs polling every few
-  // microseconds slowed the CTAs that had work (their sources and rows live
-  // in host memory too).  The kernel leaves after idle_polls x 4 us without
-  // work.  The request record is re-read only when the claimed item belongs
-  // to another request than the CTA's last one.
+  // over the chip-to-chip link.  The kernel leaves when the host sets the
+  // stop word (it does so once no work has been outstanding for idle_polls x
+  // 4 us); a CTA also leaves on its own after 100 times that without work,
+  // so that no wait is unbounded.  CTAs do not leave one by one between
+  // bursts of requests: a thinned-out grid would serve the next burst with
+  // a few CTAs.  The request record is re-read only when the claimed item
+  // belongs to another request than the CTA's last one.
   unsigned long long idle_ns = 0;
   unsigned nap = 1000;
   int last_req = -1;
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(kSrvThreads, 2) k_serve(SrvArgs S) {
     __syncthreads();
     if (!s_have) {  // CTA-uniform
       idle_ns += nap;
-      if (idle_ns > (unsigned long long)S.idle_polls * 4000ull || s_stop) break;
+      if (idle_ns > (unsigned long long)S.idle_polls * 400000ull || s_stop) break;
       if (threadIdx.x == 0) __nanosleep(nap);
       nap = min(2u * nap, 128000u);
       __syncthreads();
