@@ -16,7 +16,7 @@ e2e:   the same step through the host-buffer API: lp_graph_create from the
 roofline: the dominant scan kernel, algorithmic bytes (Gamma_a ids, degree of
        each b, the b offset of kept arcs, 4 bytes per scanned wedge) / its
        event-timed duration.
-the benchmark spec: the same measurements for R-MAT scale 24 (16,777,216 vertices,
+rmat24_dlh256: the same measurements for R-MAT scale 24 (16,777,216 vertices,
        10% held out), DLH hub limit 256, JC and RA, N_P = |E^U|.
 cpu_baseline: the CPU oracle on all host cores over the ten calls of the
        step, run once outside the timed region (about 4 minutes on 16 cores;
@@ -264,8 +264,8 @@ def run_ours(args, rank, world, local_rank):
     if args.scale != 20 or args.only:
         line["config"]["workload"] += f" [subset: scale {args.scale}, calls {args.only or 'all'}]"
     G.close()
-    if not args.no_north_star and args.scale == 20 and not args.only:
-        line["north_star"] = run_north_star(lp, torch, args)
+    if not args.no_rmat24 and args.scale == 20 and not args.only:
+        line["rmat24_dlh256"] = run_rmat24(lp, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(split, args.cpu_baseline)
     return line
@@ -304,10 +304,11 @@ def roofline(stats):
             "share_of_scan_ms": round(tier_ms[dom] / max(1e-9, sum(tier_ms)), 4)}
 
 
-def run_north_star(lp, torch, args):
-    """R-MAT scale 24 (10% held out), DLH(256) JC and RA with N_P = |E^U|:
-    the configuration the >= 50% HBM target is stated for.  Graph resident,
-    outputs in device memory, CUDA events on the library's stream."""
+def run_rmat24(lp, torch, args):
+    """R-MAT scale 24 (10% held out), DLH(256) JC and RA with N_P = |E^U|: a
+    graph whose index array is far larger than the L2, where the
+    expand-and-count tier runs.  Graph resident, outputs in device memory,
+    CUDA events on the library's stream."""
     import lp_inputs as L
     t0 = time.perf_counter()
     split = L.holdout(L.cfg_rmat24(), 0.1, seed=43)
@@ -318,7 +319,7 @@ def run_north_star(lp, torch, args):
     stream = torch.cuda.ExternalStream(G.stream)
     d_out = torch.empty((k * 16,), dtype=torch.uint8, device="cuda")
     calls = [("JC", 256), ("RA", 256)]
-    for _ in range(args.ns_warmup):
+    for _ in range(args.r24_warmup):
         for m, c in calls:
             lp.lp_predict_dev(G.handle, m, c, k, 0.0, d_out, k)
     torch.cuda.synchronize()
@@ -328,7 +329,7 @@ def run_north_star(lp, torch, args):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        for _ in range(args.ns_steps):
+        for _ in range(args.r24_steps):
             for m, c in calls:
                 total += lp.lp_predict_dev(G.handle, m, c, k, 0.0, d_out, k)
                 st = lp.lp_last_stats()
@@ -348,9 +349,9 @@ def run_north_star(lp, torch, args):
     return {"workload": "R-MAT scale 24 (16,777,216 vertices, edge factor 16, "
                         "a,b,c=0.57,0.19,0.19), 10% held out; global top-|E^U| for DLH(256) "
                         "JC and RA",
-            "edges_undirected": int(obs.edges), "N_P": k, "steps": args.ns_steps,
-            "warmup": args.ns_warmup, "ms_per_step": round(ms / args.ns_steps, 3),
-            "ms_per_call": {x: round(v / args.ns_steps, 3) for x, v in per.items()},
+            "edges_undirected": int(obs.edges), "N_P": k, "steps": args.r24_steps,
+            "warmup": args.r24_warmup, "ms_per_step": round(ms / args.r24_steps, 3),
+            "ms_per_call": {x: round(v / args.r24_steps, 3) for x, v in per.items()},
             "edges_per_s": round(total / (ms / 1e3), 1), "unit": "edges/s",
             "wedges_per_s": round(sum(s["wedges"] for s in stats) / (ms / 1e3), 1),
             "roofline": roofline(stats),
@@ -707,10 +708,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-baseline", default="full", choices=["full", "sample"],
                     help="oracle over all ten calls (full) or the cap-16 pair (sample)")
-    ap.add_argument("--no-north-star", action="store_true",
+    ap.add_argument("--no-rmat24", action="store_true",
                     help="skip the R-MAT scale-24 DLH(256) record")
-    ap.add_argument("--ns-steps", type=int, default=3, help="north_star: timed steps")
-    ap.add_argument("--ns-warmup", type=int, default=1, help="north_star: warm-up steps")
+    ap.add_argument("--r24-steps", type=int, default=3, help="rmat24_dlh256: timed steps")
+    ap.add_argument("--r24-warmup", type=int, default=1, help="rmat24_dlh256: warm-up steps")
     ap.add_argument("--only", default="", help="subset of calls, e.g. JC@inf,RA@256")
     ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (20 = the workload)")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "serve", "batch"],

@@ -1,5 +1,5 @@
 """The benchmark's JSON contract on the host (no GPU): the reference arm (the
-oracle on the host cores) prints one line with the keys the driver reads,
+oracle on the host cores) prints one JSON line with the benchmark's keys,
 and the DRAM-traffic record is used only while the kernel sources hash to
 the value stored with it."""
 import json
