@@ -264,7 +264,7 @@ def run_ours(args, rank, world, local_rank):
     if args.scale != 20 or args.only:
         line["config"]["workload"] += f" [subset: scale {args.scale}, calls {args.only or 'all'}]"
     G.close()
-    if not args.no_rmat24 and args.scale == 20 and not args.only:
+    if not args.no_rmat24 and args.scale == 20 and not args.only and world == 1:
         line["rmat24_dlh256"] = run_rmat24(lp, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(split, args.cpu_baseline)
