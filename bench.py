@@ -118,16 +118,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# the sources the global mode's kernels and their launches are built from
-# (the serving, batched and allocation-free paths are not among them)
-GLOBAL_PATH_SOURCES = ["lp_internal.cuh", "lp_scan_dev.cuh", "lp_scan.cu", "lp_expand.cu",
-                       "lp_select.cu", "lp_sort.cu", "lp_pair.cu", "lp_api.cu"]
+# the sources each measured kernel and its launches are built from
+KERNEL_SOURCES = {
+    "k_scan_big": ["lp_internal.cuh", "lp_scan_dev.cuh", "lp_scan.cu", "lp_api.cu"],
+    "k_exp_tiles+k_exp_count": ["lp_internal.cuh", "lp_scan_dev.cuh", "lp_scan.cu",
+                                "lp_expand.cu", "lp_api.cu"],
+}
 
 
-def kernel_hash() -> str:
+def kernel_hash(kernel: str = "k_scan_big") -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2401_11415_gb300", "csrc")
-    for f in GLOBAL_PATH_SOURCES:
+    for f in KERNEL_SOURCES.get(kernel, KERNEL_SOURCES["k_exp_tiles+k_exp_count"]):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -143,7 +145,7 @@ def traffic_record(kernel: str, alg_bytes_per_launch: float):
     except Exception:
         return None, None
     ent = rec.get(kernel)
-    if not ent or ent.get("kernel_hash") != kernel_hash():
+    if not ent or ent.get("kernel_hash") != kernel_hash(kernel):
         return None, None
     ratio = ent.get("dram_bytes_per_alg_byte")
     if ratio is None:

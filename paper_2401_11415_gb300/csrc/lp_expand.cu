@@ -403,7 +403,20 @@ __global__ void __launch_bounds__(kCountThreads, 3) k_exp_count(ScanArgs A, cons
           if (hc) atomicAdd(dhi + p, hc);
         }
       } else if (!guard) {
-        hash_add<V>(keys, vals, logcap, c, wc);
+        // the bucket cannot fill: claim or find the key with one compare-and-swap
+        // per probe (most keys of a hash bucket are new)
+        const u32 mask = (1u << logcap) - 1u;
+        u32 h = hash_slot(c + 1, logcap);
+        for (u32 probe = 0;; ++probe) {
+          if (probe > mask) {  // cannot happen: at most 3/4 of the slots are taken
+            A.ctr->error = 5u;
+            return;
+          }
+          const int old = atomicCAS(&keys[h], kEmpty, c + 1);
+          if (old == kEmpty || old == c + 1) break;
+          h = (h + 1u) & mask;
+        }
+        shared_add<V>(&vals[h], wc);
       } else {
         if (*(volatile int*)&s_overflow) return;
         if (hash_add<V>(keys, vals, logcap, c, wc, fill_probes(logcap)) == 2) s_overflow = 1;

@@ -46,11 +46,11 @@ def test_traffic_record_follows_kernel_hash(tmp_path, monkeypatch):
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(b, "ROOT", str(tmp_path))
     # the hash is taken over the sources under ROOT: point it back at the repository's
-    monkeypatch.setattr(b, "kernel_hash", lambda: h)
+    monkeypatch.setattr(b, "kernel_hash", lambda kernel="k_scan_big": h)
     t, basis = b.traffic_record("k_scan_big", 4000)
     assert t == 1000 and "a test" in basis
     assert b.traffic_record("k_scan_cta", 4000) == (None, None)
-    monkeypatch.setattr(b, "kernel_hash", lambda: "0" * 16)
+    monkeypatch.setattr(b, "kernel_hash", lambda kernel="k_scan_big": "0" * 16)
     assert b.traffic_record("k_scan_big", 4000) == (None, None)
 
 
